@@ -1,0 +1,368 @@
+"""Benchmark of the partitioned heat-stencil path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload heat2d|heat1d|...] [--quick]
+
+One "step" is one full pass of the headline workload: a 2D 5-point FTCS
+solve on an 8192 x 8192 FP64 Dirichlet grid cut into 64 tiles of 1024^2
+(one stream slot per tile, halo dependencies as futures), r = 0.2, 1000
+time steps, a snapshot every 100 steps whose tiles are copied to the host
+and reduced to L2 norms by host continuations while the GPU keeps stepping,
+plus device-side norms.  Each step continues the evolution of the previous
+one, so the work per step is identical.  The field (2 x 512 MiB) is larger
+than L2, so no L2 flush is needed between steps.
+
+Rank 0 prints one JSON line.  Under torchrun every rank runs an independent
+replica on its own GPU (the workload has no exchange between GPUs), and
+`value` sums the ranks' updates over the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "point-updates/s & HBM fraction of peak; graph/batched/adjoint vs plain, same GPU"
+UNIT = "point-updates/s"
+
+# headline workload
+NY = NX = 8192
+TILES = (8, 8)
+R2D = 0.2
+STEPS2D = 1000
+EVERY = 100
+# FP64 pipe operations of one 2D update: 3 adds + 2 fused multiply-adds
+OPS_PER_UPDATE_2D = 5
+BYTES_PER_UPDATE_2D = 16  # one 8-byte read and one 8-byte write
+
+
+def load_peaks():
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    peaks = {"hbm_gbs": 6400.0, "hbm_source": "fallback", "sm_max_mhz": 2032.0, "sms": 148}
+    if os.path.exists(p):
+        d = json.load(open(p))
+        peaks["hbm_gbs"] = float(d.get("hbm_gbs", 6400.0))
+        peaks["hbm_source"] = "measured"
+        peaks["sm_max_mhz"] = float(d.get("sm_max_mhz", 2032.0))
+    # FP64 pipe: 2 operations (DADD / DMUL / DFMA) per clock per SM on B300
+    peaks["fp64_gops"] = 2 * peaks["sms"] * peaks["sm_max_mhz"] / 1e3
+    return peaks
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allmax(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- our arm
+
+class Timer:
+    """CUDA events on one stream slot of the device; the slot waits for the
+    measured future before the end event is recorded."""
+
+    def __init__(self, dev, slot=0):
+        import ctypes
+        from paper_1810_11482_b300 import hxc
+        self.hxc = hxc
+        self.dev = dev
+        self.stream = dev.stream(slot)
+        self.cudart = ctypes.CDLL("libcudart.so.13")
+        self.ev = [ctypes.c_void_p(), ctypes.c_void_p()]
+        for e in self.ev:
+            assert self.cudart.cudaEventCreate(ctypes.byref(e)) == 0
+        self.ctypes = ctypes
+
+    def start(self):
+        """Records the start event and returns a future the timed work must
+        depend on."""
+        assert self.cudart.cudaEventRecord(self.ev[0], self.stream) == 0
+        out = self.hxc.c_fut()
+        self.hxc.check(self.hxc.lib().hxc_future_from_stream(self.dev.h, self.stream,
+                                                            self.ctypes.byref(out)))
+        return self.hxc.Future(out.value)
+
+    def stop(self, fut):
+        self.hxc.check(self.hxc.lib().hxc_future_stream_wait(fut.h, self.stream))
+        assert self.cudart.cudaEventRecord(self.ev[1], self.stream) == 0
+        assert self.cudart.cudaEventSynchronize(self.ev[1]) == 0
+        ms = self.ctypes.c_float()
+        assert self.cudart.cudaEventElapsedTime(self.ctypes.byref(ms), self.ev[0], self.ev[1]) == 0
+        return ms.value
+
+
+def ours(args, world, rank, local, pg):
+    from paper_1810_11482_b300 import hxc, synth
+    devs = hxc.get_all_devices(2, 0)
+    if not devs:
+        raise RuntimeError("no CUDA device visible")
+    dev = devs[local % len(devs)]
+    peaks = load_peaks()
+    T = TILES[0] * TILES[1]
+    nsnap = STEPS2D // EVERY
+    u0 = synth.bumps2d(NY, NX, seed=2)
+    field = u0.nbytes
+    u, tmp = dev.buffer(field), dev.buffer(field)
+    u.write(u0).get()
+    hn = np.zeros(nsnap * T)
+    gn = np.zeros(nsnap * T)
+    upd = NY * NX * STEPS2D
+    timer = Timer(dev, 0)
+    launches = [0]
+
+    def one(mode, deps=()):
+        cfg = hxc.heat2d_cfg(NY, NX, TILES[0], TILES[1], R2D, STEPS2D, EVERY, mode, hn, gn)
+        f, fr, st = hxc.heat2d_run(dev, u, tmp, cfg, deps, field_ready=True)
+        launches[0] += st.kernel_launches
+        return f, fr
+
+    def timed(mode, k, w):
+        for _ in range(w):
+            f, _ = one(mode)
+            f.get()
+        dev.synchronize()
+        barrier(pg)
+        launches[0] = 0
+        start = timer.start()
+        ready = start
+        alls = []
+        for _ in range(k):
+            # the next pass starts as soon as the field is final; the host
+            # norms of this pass overlap with it
+            f, ready = one(mode, deps=[ready])
+            alls.append(f)
+        ms = timer.stop(hxc.when_all(alls))
+        barrier(pg)
+        return ms, launches[0]
+
+    best_mode = args.mode
+    clocks = Clocks(local)
+    clocks.start()
+    ms, n_launch = timed(best_mode, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_max = allmax(pg, ms)
+    total_upd = allsum(pg, upd * args.steps)
+    value = total_upd / (ms_max / 1e3)
+
+    # per-mode comparison (plain per-partition launches vs graph vs fused)
+    modes = {}
+    if not args.quick:
+        for mode in ("plain", "graph", "fused"):
+            mms, ml = timed(mode, 1, 1)
+            modes[mode] = {"updates_per_s": upd / (mms / 1e3), "ms": mms, "launches": ml}
+
+    # roofline of the dominant kernel: back-to-back whole-domain step launches
+    rsteps = 200
+    cfg = hxc.heat2d_cfg(NY, NX, 1, 1, R2D, rsteps, 0, "fused", None, None)
+    f, _ = hxc.heat2d_run(dev, u, tmp, cfg)
+    f.get()
+    start = timer.start()
+    f, st = hxc.heat2d_run(dev, u, tmp, cfg, deps=[start])
+    kms = timer.stop(f) / rsteps
+    upd_launch = NY * NX
+    ach_gops = upd_launch * OPS_PER_UPDATE_2D / (kms / 1e3) / 1e9
+    ach_gbs = upd_launch * BYTES_PER_UPDATE_2D / (kms / 1e3) / 1e9
+    traffic = None
+    tp = os.path.join(HERE, "profiles", "heat2d_traffic.json")
+    if os.path.exists(tp):
+        traffic = json.load(open(tp)).get("bytes_per_launch")
+    roof = {"bound": "alu", "achieved": ach_gops, "peak": peaks["fp64_gops"], "unit": "Gop/s",
+            "frac": ach_gops / peaks["fp64_gops"], "traffic": traffic,
+            "kernel": "k_heat2d<2> (whole 8192^2 field, one step per launch)",
+            "ms_per_launch": kms,
+            "peak_source": "FP64 pipe: 2 ops/clk/SM x 148 SMs x %.0f MHz" % peaks["sm_max_mhz"],
+            "hbm": {"achieved_gbs": ach_gbs, "peak_gbs": peaks["hbm_gbs"],
+                    "frac": ach_gbs / peaks["hbm_gbs"], "peak_source": peaks["hbm_source"]}}
+
+    # end to end through the host entry point: pinned host field in and out
+    e2e = None
+    if not args.quick:
+        hu = hxc.host_empty((NY, NX))
+        hu[:] = u0
+        ho = hxc.host_empty((NY, NX))
+        cfg = hxc.heat2d_cfg(NY, NX, TILES[0], TILES[1], R2D, STEPS2D, EVERY, best_mode, hn, gn)
+        hxc.heat2d_run_host(dev, hu.ctypes.data, ho.ctypes.data, cfg)  # warm-up
+        k = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            st = hxc.heat2d_run_host(dev, hu.ctypes.data, ho.ctypes.data, cfg)
+        el = time.perf_counter() - t0
+        el = allmax(pg, el)
+        e2e = {"value": allsum(pg, upd * k) / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(st.h2d_bytes), "d2h_bytes_per_step": int(st.d2h_bytes),
+               "steps": k}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "heat2d FTCS 8192x8192 FP64, 64 tiles of 1024^2, r=0.2, "
+                               "1000 steps, snapshot+host L2 norms every 100 steps",
+                   "mode": best_mode, "parallelism": "replicas x%d" % world,
+                   "l2": "field 2x512 MiB > 126 MB L2 (no flush needed)"},
+        "roofline": roof, "gpu_launches": int(allsum(pg, n_launch)), "modes": modes,
+        "clocks": clk, "e2e": e2e,
+    }
+    return out
+
+
+def cpu_baseline(sample_steps=3):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    headline workload: the full 8192^2 field advanced `sample_steps` steps."""
+    import oracle
+    from paper_1810_11482_b300 import synth
+    u0 = synth.bumps2d(NY, NX, seed=2)
+    oracle.heat2d(u0[:64, :64], R2D, 1)  # load/compile
+    t0 = time.perf_counter()
+    oracle.heat2d(u0, R2D, sample_steps)
+    el = time.perf_counter() - t0
+    return {"value": NY * NX * sample_steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "full 8192^2 field, %d of the 1000 steps (single-threaded C, -O2, no FMA)"
+                      % sample_steps, "seconds": el}
+
+
+def reference(args, world, rank):
+    if rank != 0:
+        return None
+    steps = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(1)
+        if i >= args.warmup:
+            steps.append(b["seconds"])
+        base = b
+    per = statistics.mean(steps)
+    value = NY * NX / per
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "heat2d FTCS 8192x8192 FP64, 64 tiles of 1024^2, r=0.2, "
+                                   "1000 steps, snapshot+host L2 norms every 100 steps",
+                       "sample": "each step: the full field advanced 1 time step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "full 8192^2 field, 1 time step per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fused", choices=["plain", "graph", "fused"])
+    ap.add_argument("--quick", action="store_true", help="skip mode comparison and e2e")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local, pg = dist_setup(args.gpus)
+    if args.impl == "reference":
+        out = reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = ours(args, world, rank, local, pg)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

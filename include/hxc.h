@@ -1,0 +1,365 @@
+/*
+ * hxc.h -- C ABI of the B300 heat-stencil library.
+ *
+ * The calls follow the paper's programming model (Sec. 3.1 "Futurization",
+ * Sec. 4 "Design of the implementation"): a device owns asynchronous work
+ * queues, a buffer is device memory with asynchronous copies to and from the
+ * host, a kernel launch takes buffers as arguments, and every asynchronous
+ * call returns a future that later calls take as dependencies and that host
+ * code composes with then / when_all / wait_all.  The work carried by those
+ * futures is the explicit (forward-time, centred-space) heat stencil in
+ * 1D/2D/3D, a batched variable-diffusivity form and its discrete adjoint.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Status.  Every call returns hxc_status.  Argument errors are reported
+ *    synchronously and create no future.  Errors of asynchronous work (a
+ *    CUDA error, a failing host continuation) are stored in the future of
+ *    that work; an operation whose dependency failed does not run and its
+ *    future holds HXC_E_DEP_FAILED.  hxc_last_error() gives a thread-local
+ *    description of the last synchronous error.
+ *  - Handles (hxc_device, hxc_buffer, hxc_future, hxc_graph) are opaque and
+ *    reference counted.  The caller releases each handle it receives exactly
+ *    once.  A future keeps the buffers its operation uses alive until the
+ *    future itself is released.
+ *  - Host pointers given to asynchronous copies must stay valid and
+ *    unmodified until the copy's future is ready (as for cudaMemcpyAsync).
+ *    Page-locked memory from hxc_host_alloc overlaps with other work;
+ *    pageable memory is accepted but the copy may be staged.
+ *  - Stream slots.  A device has up to HXC_MAX_SLOTS asynchronous queues
+ *    (CUDA streams, created on first use).  Work on one slot runs in issue
+ *    order; work on different slots is ordered only by futures.
+ *  - Threads.  All calls are thread-safe, except that while a device is
+ *    capturing a graph only the capturing thread may issue work to it.
+ *    Host continuations run on an internal worker pool, never on CUDA's
+ *    callback thread.
+ *  - Waits are bounded: hxc_future_wait takes a timeout; device kernels that
+ *    spin on a flag give up after a bounded number of polls and report
+ *    HXC_E_TIMEOUT through their status word.
+ *
+ * Data layouts
+ *  - 1D fields: n contiguous doubles, periodic.
+ *  - 2D fields: row-major ny x nx doubles, element (i, j) = (y, x) at
+ *    i * nx + j, Dirichlet-zero ghost ring outside the field.
+ *  - 3D fields: nz x ny x nx floats, x fastest, periodic.
+ *  - Batches: problems packed back to back, problem p a row-major side_p x
+ *    side_p block starting at element offset_p.
+ */
+#ifndef HXC_H
+#define HXC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HXC_MAX_SLOTS 256
+#define HXC_ABI_VERSION 1
+
+typedef struct hxc_device_t *hxc_device;
+typedef struct hxc_buffer_t *hxc_buffer;
+typedef struct hxc_future_t *hxc_future;
+typedef struct hxc_graph_t *hxc_graph;
+
+typedef enum {
+    HXC_OK = 0,
+    HXC_E_INVALID = 1,      /* bad argument or handle                         */
+    HXC_E_NOMEM = 2,        /* device or host allocation failed               */
+    HXC_E_CUDA = 3,         /* CUDA runtime error (see hxc_last_error)         */
+    HXC_E_TIMEOUT = 4,      /* a bounded wait ran out                         */
+    HXC_E_DEP_FAILED = 5,   /* a dependency failed; this operation did not run */
+    HXC_E_CALLBACK = 6,     /* a host continuation returned an error          */
+    HXC_E_UNSUPPORTED = 7,  /* valid request this build does not support      */
+    HXC_E_NODEV = 8         /* no CUDA device satisfies the request           */
+} hxc_status;
+
+/* Host continuation for hxc_future_then: runs on the worker pool once the
+ * antecedent future is ready and succeeded.  Returning anything other than
+ * HXC_OK stores HXC_E_CALLBACK in the continuation's future. */
+typedef hxc_status (*hxc_host_fn)(void *user);
+
+/* Launch configuration (Listing 2 exposes grid and block to the user,
+ * Sec. 4.2).  Passing NULL lets the library choose (autotuned).  Every
+ * built-in kernel is correct for any grid (grid-stride loops); the block
+ * must be a multiple of 32 threads within the kernel's supported range. */
+typedef struct {
+    uint32_t grid[3];
+    uint32_t block[3];
+} hxc_launch_cfg;
+
+/* ------------------------------------------------------------------ status */
+
+const char *hxc_status_string(hxc_status s);
+/* Thread-local text of the last synchronous error of this thread (never NULL). */
+const char *hxc_last_error(void);
+int hxc_abi_version(void);
+/* Drains the worker pool and joins its threads.  Optional; call before
+ * process exit when continuations may still be running. */
+hxc_status hxc_shutdown(void);
+
+/* ----------------------------------------------------------------- devices */
+
+/* Sec. 4.1, Listing 1: all local CUDA devices whose compute capability is at
+ * least (min_major, min_minor).  Writes up to `cap` new device handles to
+ * `out` and the number of matching devices to *n_out.  Remote devices of the
+ * paper's distributed setting are not supported (single node, single GPU).
+ * Returns HXC_E_NODEV when no device matches. */
+hxc_status hxc_get_all_devices(int min_major, int min_minor, hxc_device *out, int cap,
+                               int *n_out);
+/* Compute capability, SM count and global memory of a device. */
+hxc_status hxc_device_info(hxc_device dev, int *major, int *minor, int *sm_count,
+                           size_t *global_mem);
+/* Blocks until every slot of the device is idle (cudaDeviceSynchronize
+ * semantics restricted to this library's streams). */
+hxc_status hxc_device_synchronize(hxc_device dev);
+/* The CUDA stream (cudaStream_t) behind a slot, created if needed. */
+hxc_status hxc_device_stream(hxc_device dev, int slot, void **stream);
+hxc_status hxc_device_retain(hxc_device dev);
+hxc_status hxc_device_release(hxc_device dev);
+
+/* ----------------------------------------------------------- host memory */
+
+/* Page-locked host allocation (Listing 2 allocates its host data with
+ * cudaMallocHost).  Free with hxc_host_free. */
+hxc_status hxc_host_alloc(size_t bytes, void **p);
+hxc_status hxc_host_free(void *p);
+
+/* ----------------------------------------------------------------- buffers */
+
+/* Sec. 4, "buffer": `bytes` of device memory on `dev` (cudaMalloc, Listing 2
+ * line "create_buffer").  Contents are undefined until written. */
+hxc_status hxc_device_create_buffer(hxc_device dev, size_t bytes, hxc_buffer *out);
+/* Wraps existing device memory (for example a torch tensor) without taking
+ * ownership: the memory must outlive the buffer and every future using it. */
+hxc_status hxc_buffer_wrap(hxc_device dev, void *device_ptr, size_t bytes, hxc_buffer *out);
+hxc_status hxc_buffer_device_ptr(hxc_buffer buf, void **device_ptr, size_t *bytes);
+hxc_status hxc_buffer_retain(hxc_buffer buf);
+hxc_status hxc_buffer_release(hxc_buffer buf);
+
+/* Asynchronous host->device copy of `bytes` from `host` into the buffer at
+ * byte offset `off` (Listing 2 "enqueue_write", cudaMemcpyAsync).  Runs on
+ * stream slot `slot` after every future in deps[0..ndeps) is ready. */
+hxc_status hxc_buffer_enqueue_write(hxc_buffer buf, size_t off, size_t bytes, const void *host,
+                                    int slot, const hxc_future *deps, int ndeps,
+                                    hxc_future *out);
+/* Asynchronous device->host copy (Listing 2 "enqueue_read"). */
+hxc_status hxc_buffer_enqueue_read(hxc_buffer buf, size_t off, size_t bytes, void *host,
+                                   int slot, const hxc_future *deps, int ndeps,
+                                   hxc_future *out);
+/* Synchronous read (Listing 2 "enqueue_read_sync"): enqueue, then wait
+ * without a time limit. */
+hxc_status hxc_buffer_enqueue_read_sync(hxc_buffer buf, size_t off, size_t bytes, void *host,
+                                        int slot, const hxc_future *deps, int ndeps);
+/* Asynchronous device->device copy between buffers of the same device. */
+hxc_status hxc_buffer_enqueue_copy(hxc_buffer dst, size_t dst_off, hxc_buffer src,
+                                   size_t src_off, size_t bytes, int slot,
+                                   const hxc_future *deps, int ndeps, hxc_future *out);
+/* Asynchronous strided 2D copies: `rows` rows of `row_bytes` bytes; the
+ * buffer side starts at byte offset `off` with pitch `buf_pitch`, the host
+ * side at `host` with pitch `host_pitch` (cudaMemcpy2DAsync). */
+hxc_status hxc_buffer_enqueue_write_2d(hxc_buffer buf, size_t off, size_t buf_pitch,
+                                       const void *host, size_t host_pitch, size_t row_bytes,
+                                       size_t rows, int slot, const hxc_future *deps,
+                                       int ndeps, hxc_future *out);
+hxc_status hxc_buffer_enqueue_read_2d(hxc_buffer buf, size_t off, size_t buf_pitch,
+                                      void *host, size_t host_pitch, size_t row_bytes,
+                                      size_t rows, int slot, const hxc_future *deps,
+                                      int ndeps, hxc_future *out);
+
+/* ----------------------------------------------------------------- futures */
+
+/* Sec. 3.1: futures compose with then and when_all; wait_all is a barrier.
+ * A future is ready when its operation finished; its status is then final. */
+hxc_status hxc_future_is_ready(hxc_future f, int *ready);
+/* Waits up to timeout_ns nanoseconds (< 0: no limit).  Returns the future's
+ * final status, or HXC_E_TIMEOUT if it did not become ready in time (the
+ * future stays valid and may be waited on again). */
+hxc_status hxc_future_wait(hxc_future f, int64_t timeout_ns);
+/* Waits for every future (Listing 2 "wait_all"); returns the first
+ * non-OK status in array order, HXC_E_TIMEOUT if the time ran out. */
+hxc_status hxc_wait_all(const hxc_future *fs, int n, int64_t timeout_ns);
+/* Attaches a host continuation (Sec. 3.1 "then").  `out` becomes ready with
+ * fn's status after fn returned; fn does not run if f failed. */
+hxc_status hxc_future_then(hxc_future f, hxc_host_fn fn, void *user, hxc_future *out);
+/* Joins futures (Sec. 3.1 "when_all").  When every input is device work the
+ * join is done on the device (no host round trip). */
+hxc_status hxc_when_all(const hxc_future *fs, int n, hxc_future *out);
+/* An already-ready future holding `status`. */
+hxc_status hxc_make_ready_future(hxc_status status, hxc_future *out);
+/* A future completed later by hxc_promise_set (host-side producer). */
+hxc_status hxc_promise_create(hxc_future *out);
+hxc_status hxc_promise_set(hxc_future promise, hxc_status status);
+/* Interop with foreign CUDA streams (e.g. torch's current stream):
+ * a future for everything issued so far on `stream` ... */
+hxc_status hxc_future_from_stream(hxc_device dev, void *stream, hxc_future *out);
+/* ... and making `stream` wait for a future (device-side, no host wait). */
+hxc_status hxc_future_stream_wait(hxc_future f, void *stream);
+hxc_status hxc_future_retain(hxc_future f);
+hxc_status hxc_future_release(hxc_future f);
+
+/* --------------------------------------------------------- kernel launches */
+
+/* Built-in kernels (the paper's "program.run(args, name, grid, block)",
+ * Sec. 4.2, with a fixed kernel table instead of run-time compilation). */
+typedef enum {
+    /* Listing 2: result[0] = sum of n uint32 values (64-bit result). */
+    HXC_K_SUM_U32 = 1,
+    /* Sec. 5.1.1: out_i = 0.5 in_{i-1} + in_i + 0.5 in_{i+1}, periodic. */
+    HXC_K_PRK_STENCIL = 2,
+    /* 1D FTCS: dst[lo, lo+count) = `steps` periodic steps of src.  steps > 1
+     * reads a halo of width `steps` from src (temporal blocking). */
+    HXC_K_HEAT1D = 3,
+    /* 2D FTCS step on the tile [y0, y0+ty) x [x0, x0+tx). */
+    HXC_K_HEAT2D = 4,
+    /* Tile snapshot and squared norm: copies the tile of src into the compact
+     * ty x tx buffer snap (optional) and stores sum(u^2) of the tile in
+     * sums[sum_index] with a fixed reduction order. */
+    HXC_K_TILE_NORM2 = 5,
+    /* 3D FTCS, FP32, `steps` (1..4) fused steps per launch. */
+    HXC_K_HEAT3D = 6,
+    /* Variable-diffusivity FTCS step (flux form, arithmetic face mean). */
+    HXC_K_VARCOEF2D = 7,
+    /* Adjoint step with kappa-gradient accumulation. */
+    HXC_K_ADJOINT2D = 8,
+    /* Sec. 5.1.2 partition kernel: out_i = sqrt(sin(i)^2 + cos(i)^2). */
+    HXC_K_PARTITION = 9
+} hxc_kernel_id;
+
+typedef struct { hxc_buffer input, result; int64_t n; } hxc_sum_args;
+typedef struct { hxc_buffer in, out; int64_t n; } hxc_prk_args;
+typedef struct {
+    hxc_buffer src, dst;
+    int64_t n, lo, count;  /* field length, first updated point, points updated */
+    double r;              /* diffusion number dt/h^2 (stable for r <= 1/2) */
+    int32_t steps;         /* >= 1 */
+} hxc_heat1d_args;
+typedef struct {
+    hxc_buffer src, dst;
+    int64_t ny, nx;        /* field shape */
+    int64_t y0, x0, ty, tx; /* updated tile */
+    double r;              /* stable for r <= 1/4 */
+} hxc_heat2d_args;
+typedef struct {
+    hxc_buffer src, snap, sums; /* snap may be NULL */
+    int64_t ny, nx, y0, x0, ty, tx;
+    int64_t sum_index;     /* element of sums (doubles) receiving sum(u^2) */
+} hxc_tile_norm2_args;
+typedef struct {
+    hxc_buffer src, dst;
+    int64_t nz, ny, nx;
+    float r;               /* stable for r <= 1/6 */
+    int32_t steps;         /* 1..4 */
+} hxc_heat3d_args;
+typedef struct {
+    hxc_buffer src, dst, kappa;
+    int64_t ny, nx;
+    double c;              /* dt/h^2; stable for c * sum_f k_f <= 1 */
+} hxc_varcoef2d_args;
+typedef struct {
+    hxc_buffer lam_in, lam_out, u, kappa, grad_kappa;
+    int64_t ny, nx;
+    double c;
+} hxc_adjoint2d_args;
+typedef struct { hxc_buffer out; int64_t n, offset; } hxc_partition_args;
+
+/* Launches kernel `id` with the argument struct `args` (of size args_size,
+ * which must equal the struct's size) on stream slot `slot` after deps. */
+hxc_status hxc_launch(hxc_device dev, hxc_kernel_id id, const void *args, size_t args_size,
+                      const hxc_launch_cfg *cfg, int slot, const hxc_future *deps, int ndeps,
+                      hxc_future *out);
+
+/* ------------------------------------------------------------------ graphs */
+
+/* Captures every operation subsequently issued to `dev` by this thread into
+ * a CUDA graph.  Futures created during capture may be used as dependencies
+ * inside the capture only.  Dependencies from before the capture must be
+ * ready.  Host continuations cannot be captured (HXC_E_UNSUPPORTED). */
+hxc_status hxc_graph_begin(hxc_device dev);
+hxc_status hxc_graph_end(hxc_device dev, hxc_graph *out);
+/* Replays the graph on slot `slot` after deps. */
+hxc_status hxc_graph_launch(hxc_graph g, int slot, const hxc_future *deps, int ndeps,
+                            hxc_future *out);
+hxc_status hxc_graph_node_count(hxc_graph g, size_t *nodes);
+hxc_status hxc_graph_release(hxc_graph g);
+
+/* ------------------------------------------------- whole-run entry points */
+
+typedef enum {
+    /* one launch per partition and step, ordered by futures (baseline) */
+    HXC_MODE_PLAIN = 0,
+    /* the same operations captured once into a CUDA graph and replayed */
+    HXC_MODE_GRAPH = 1,
+    /* fewest launches: temporal blocking / whole-domain / persistent kernels */
+    HXC_MODE_FUSED = 2
+} hxc_mode;
+
+/* Counters filled by the run entry points (optional). */
+typedef struct {
+    int64_t kernel_launches;   /* kernels launched by the host (graph replays count their nodes) */
+    int64_t graph_launches;
+    int64_t copies;
+    int64_t host_tasks;        /* host continuations run */
+    int64_t h2d_bytes, d2h_bytes;
+} hxc_run_stats;
+
+/* 1D periodic FTCS over n points in `parts` equal partitions: `steps` steps
+ * with diffusion number r.  u holds the initial field and receives the
+ * result; tmp is scratch of the same size.  Each partition reads a halo from
+ * its neighbours: in PLAIN and GRAPH mode step s of partition p runs after
+ * step s-1 of p-1, p and p+1; FUSED mode advances `steps_per_launch` steps
+ * per launch (0: all steps in one launch).  Results are bit-identical for
+ * every partition count and mode. */
+hxc_status hxc_heat1d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, int64_t n, int parts,
+                          double r, int steps, hxc_mode mode, int steps_per_launch,
+                          const hxc_future *deps, int ndeps, hxc_future *out,
+                          hxc_run_stats *stats);
+
+typedef struct {
+    int64_t ny, nx;            /* field shape */
+    int64_t tiles_y, tiles_x;  /* partition grid; tiles may be ragged */
+    double r;
+    int32_t steps;
+    int32_t snapshot_every;    /* 0: no snapshots */
+    hxc_mode mode;
+    /* Outputs, row-major [n_snapshots][tiles_y * tiles_x] (may be NULL):
+     * host_norms: sqrt(sum u^2) per tile computed on the host from a
+     *   device->host snapshot, as then-continuations overlapping the steps;
+     * gpu_norms: the same norms reduced on the device. */
+    double *host_norms;
+    double *gpu_norms;
+} hxc_heat2d_cfg;
+
+/* 2D Dirichlet FTCS on device buffers: u (initial field, receives the
+ * result) and tmp (scratch), each ny * nx doubles.  Snapshots are taken
+ * after steps k * snapshot_every (k = 1, 2, ...).  *out becomes ready when
+ * everything, host norms included, is done; *field_ready (optional) as soon
+ * as u holds the result, possibly before the host norms finish.  The cfg
+ * struct is copied; the norm arrays must stay valid until *out is ready.
+ * When a dependency is unfinished host work the whole run is issued later
+ * by the worker pool (stats then count nothing). */
+hxc_status hxc_heat2d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, const hxc_heat2d_cfg *cfg,
+                          const hxc_future *deps, int ndeps, hxc_future *out,
+                          hxc_future *field_ready, hxc_run_stats *stats);
+/* The same run with a host-resident field: host_u0 is copied in tile by
+ * tile, the result is copied out tile by tile into host_uT (may alias
+ * host_u0).  Synchronous: returns when host_uT and the norms are written. */
+hxc_status hxc_heat2d_run_host(hxc_device dev, const double *host_u0, double *host_uT,
+                               const hxc_heat2d_cfg *cfg, hxc_run_stats *stats);
+
+/* 3D periodic FTCS in FP32 on an nz x ny x nx field (x fastest): u holds
+ * the initial field and receives the result, tmp is scratch of the same
+ * size.  PLAIN launches one step at a time, FUSED advances
+ * `steps_per_launch` (1..4, 0 = 4) steps per launch with temporal blocking,
+ * GRAPH captures the fused launches once and replays them.  All modes give
+ * bit-identical results. */
+hxc_status hxc_heat3d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, int64_t nz, int64_t ny,
+                          int64_t nx, float r, int steps, hxc_mode mode, int steps_per_launch,
+                          const hxc_future *deps, int ndeps, hxc_future *out,
+                          hxc_run_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HXC_H */

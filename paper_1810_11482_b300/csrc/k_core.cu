@@ -1,0 +1,344 @@
+// Core kernels: Listing 2 sum, PRK stencil, partition kernel, 1D and 2D
+// FTCS steps and the tile snapshot/norm reduction.
+//
+// Canonical arithmetic.  Every kernel variant (per-step, temporally blocked,
+// any tile shape, any launch order) evaluates one update with exactly the
+// same sequence of correctly rounded FP64 operations, so results are
+// bit-identical across partition counts, schedules and graph replay:
+//   1D: s = ul + ur;                 t = fma(-2, u, s); u' = fma(r, t, u)
+//   2D: s = (uW + uE) + (uN + uS);   t = fma(-4, u, s); u' = fma(r, t, u)
+// The neighbour sums are symmetric, so mirrored inputs give mirrored bits.
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace hxc {
+namespace k {
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int d = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+static inline unsigned grid_from(const hxc_launch_cfg *cfg, int64_t want) {
+    if (cfg) return cfg->grid[0] * cfg->grid[1] * cfg->grid[2];
+    if (want < 1) want = 1;
+    return (unsigned)std::min<int64_t>(want, 1 << 20);
+}
+static inline unsigned block_from(const hxc_launch_cfg *cfg, unsigned dflt) {
+    if (cfg) return cfg->block[0] * cfg->block[1] * cfg->block[2];
+    return dflt;
+}
+
+__device__ __forceinline__ double ftcs3(double ul, double u, double ur, double r) {
+    double s = __dadd_rn(ul, ur);
+    double t = __fma_rn(-2.0, u, s);
+    return __fma_rn(r, t, u);
+}
+
+__device__ __forceinline__ double ftcs5(double u, double w, double e, double n, double so,
+                                        double r) {
+    double s = __dadd_rn(__dadd_rn(w, e), __dadd_rn(n, so));
+    double t = __fma_rn(-4.0, u, s);
+    return __fma_rn(r, t, u);
+}
+
+// ------------------------------------------------------------ Listing 2 sum
+__global__ void k_sum_u32(const uint32_t *__restrict__ in, unsigned long long *result,
+                          int64_t n) {
+    unsigned long long acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += in[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(result, acc);
+}
+
+cudaError_t sum_u32(const uint32_t *in, unsigned long long *result, int64_t n,
+                    const hxc_launch_cfg *cfg, cudaStream_t s) {
+    unsigned b = block_from(cfg, 256), g = grid_from(cfg, std::min<int64_t>((n + b - 1) / b, sm_count() * 4));
+    k_sum_u32<<<g, b, 0, s>>>(in, result, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- Sec. 5.1.1 PRK
+__global__ void k_prk(const double *__restrict__ in, double *__restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double xl = in[i == 0 ? n - 1 : i - 1], xr = in[i == n - 1 ? 0 : i + 1];
+        out[i] = __dadd_rn(__dadd_rn(__dmul_rn(0.5, xl), in[i]), __dmul_rn(0.5, xr));
+    }
+}
+
+cudaError_t prk(const double *in, double *out, int64_t n, const hxc_launch_cfg *cfg,
+                cudaStream_t s) {
+    unsigned b = block_from(cfg, 256), g = grid_from(cfg, std::min<int64_t>((n + b - 1) / b, sm_count() * 8));
+    k_prk<<<g, b, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- Sec. 5.1.2 partition k
+__global__ void k_partition(double *__restrict__ out, int64_t n, int64_t offset) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double x = (double)(offset + i);
+        double sv = sin(x), cv = cos(x);
+        out[i] = sqrt(sv * sv + cv * cv);
+    }
+}
+
+cudaError_t partition(double *out, int64_t n, int64_t offset, const hxc_launch_cfg *cfg,
+                      cudaStream_t s) {
+    unsigned b = block_from(cfg, 256), g = grid_from(cfg, std::min<int64_t>((n + b - 1) / b, sm_count() * 8));
+    k_partition<<<g, b, 0, s>>>(out, n, offset);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ 1D FTCS
+__global__ void k_heat1d_step(const double *__restrict__ src, double *__restrict__ dst,
+                              int64_t n, int64_t lo, int64_t count, double r) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = lo + t;
+        int64_t jl = j == 0 ? n - 1 : j - 1, jr = j == n - 1 ? 0 : j + 1;
+        dst[j] = ftcs3(src[jl], src[j], src[jr], r);
+    }
+}
+
+// Temporally blocked 1D FTCS: a CTA loads its chunk of C points plus a halo of
+// T points on each side (wrapping periodically) into shared memory, advances
+// T steps there (the valid window shrinks by one point per side per step)
+// and writes its C points.  Chunks are visited grid-stride.
+__global__ void k_heat1d_tb(const double *__restrict__ src, double *__restrict__ dst, int64_t n,
+                            int64_t lo, int64_t count, double r, int T, int C) {
+    extern __shared__ double sm[];
+    const int W = C + 2 * T;
+    double *a = sm, *b = sm + W;
+    for (int64_t c0 = (int64_t)blockIdx.x * C; c0 < count; c0 += (int64_t)gridDim.x * C) {
+        int64_t base = lo + c0 - T;
+        bool wraps = base < 0 || base + W > n;
+        for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            int64_t g = base + i;
+            if (wraps) {
+                g %= n;
+                if (g < 0) g += n;
+            }
+            a[i] = src[g];
+        }
+        __syncthreads();
+        double *pa = a, *pb = b;
+        for (int s = 1; s <= T; s++) {
+            for (int i = s + threadIdx.x; i < W - s; i += blockDim.x)
+                pb[i] = ftcs3(pa[i - 1], pa[i], pa[i + 1], r);
+            __syncthreads();
+            double *t = pa;
+            pa = pb;
+            pb = t;
+        }
+        int cnt = (int)(count - c0 < (int64_t)C ? count - c0 : (int64_t)C);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) dst[lo + c0 + i] = pa[T + i];
+        __syncthreads();
+    }
+}
+
+cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
+                   double r, int steps, const hxc_launch_cfg *cfg, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (steps == 1) {
+        unsigned b = block_from(cfg, 256);
+        unsigned g = grid_from(cfg, std::min<int64_t>((count + b - 1) / b, sm_count() * 8));
+        k_heat1d_step<<<g, b, 0, s>>>(src, dst, n, lo, count, r);
+        return cudaGetLastError();
+    }
+    unsigned b = block_from(cfg, 512);
+    unsigned g = grid_from(cfg, sm_count());
+    // chunk per CTA: spread `count` over the grid, bounded by shared memory
+    const int64_t max_w = (200 * 1024) / (2 * sizeof(double));
+    int64_t C = (count + g - 1) / g;
+    C = (C + 15) / 16 * 16;
+    if (C + 2 * steps > max_w) C = std::max<int64_t>(16, (max_w - 2 * steps) / 16 * 16);
+    if (C + 2 * steps > max_w) return cudaErrorInvalidValue;
+    size_t smem = 2 * (size_t)(C + 2 * steps) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_heat1d_tb, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = true;
+    }
+    k_heat1d_tb<<<g, b, smem, s>>>(src, dst, n, lo, count, r, steps, (int)C);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ 2D FTCS
+// A warp owns a strip of 32*V columns (V consecutive columns per lane) and
+// `H` rows, walks the rows keeping rows y-1, y, y+1 in registers, and gets
+// its x-neighbours from the adjacent lanes by shuffles; the two columns just
+// outside the strip are read from global memory (zero outside the field).
+template <int V>
+struct Vec;
+template <>
+struct Vec<1> {
+    double a;
+};
+template <>
+struct Vec<2> {
+    double a, b;
+};
+
+template <int V>
+__device__ __forceinline__ void load_row(Vec<V> &v, const double *__restrict__ src, int64_t ny,
+                                         int64_t nx, int64_t y, int64_t x, bool active) {
+    if (active && y >= 0 && y < ny) {
+        if constexpr (V == 2) {
+            double2 q = __ldg(reinterpret_cast<const double2 *>(src + y * nx + x));
+            v.a = q.x;
+            v.b = q.y;
+        } else {
+            v.a = __ldg(src + y * nx + x);
+        }
+    } else {
+        v.a = 0.0;
+        if constexpr (V == 2) v.b = 0.0;
+    }
+}
+
+__device__ __forceinline__ double at2(const double *__restrict__ src, int64_t ny, int64_t nx,
+                                      int64_t y, int64_t x) {
+    return (y >= 0 && y < ny && x >= 0 && x < nx) ? __ldg(src + y * nx + x) : 0.0;
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_heat2d(const double *__restrict__ src,
+                                                double *__restrict__ dst, int64_t ny, int64_t nx,
+                                                int64_t y0, int64_t x0, int64_t ty, int64_t tx,
+                                                double r, int H) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t SW = 32 * V;
+    const int64_t nsx = (tx + SW - 1) / SW, nsy = (ty + H - 1) / H;
+    const int64_t nwork = nsx * nsy;
+    for (int64_t w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nwork; w += (int64_t)gridDim.x * wpb) {
+        const int64_t sx = w % nsx, sy = w / nsx;
+        const int64_t xs = x0 + sx * SW, xe = min(x0 + tx, xs + SW);
+        const int64_t ys = y0 + sy * H, ye = min(y0 + ty, ys + H);
+        const int64_t xl = xs + (int64_t)lane * V;
+        const bool active = xl < xe;
+        const bool last = active && xl + V >= xe;  // owns the strip's last column
+        Vec<V> prv, cur, nxt;
+        load_row<V>(prv, src, ny, nx, ys - 1, xl, active);
+        load_row<V>(cur, src, ny, nx, ys, xl, active);
+        for (int64_t y = ys; y < ye; y++) {
+            load_row<V>(nxt, src, ny, nx, y + 1, xl, active);
+            double hi;
+            if constexpr (V == 2)
+                hi = cur.b;
+            else
+                hi = cur.a;
+            double left = __shfl_up_sync(0xffffffffu, hi, 1);
+            double right = __shfl_down_sync(0xffffffffu, cur.a, 1);
+            if (lane == 0) left = at2(src, ny, nx, y, xs - 1);
+            if (last) right = at2(src, ny, nx, y, xl + V);
+            if (active) {
+                if constexpr (V == 2) {
+                    double2 o;
+                    o.x = ftcs5(cur.a, left, cur.b, prv.a, nxt.a, r);
+                    o.y = ftcs5(cur.b, cur.a, right, prv.b, nxt.b, r);
+                    *reinterpret_cast<double2 *>(dst + y * nx + xl) = o;
+                } else {
+                    dst[y * nx + xl] = ftcs5(cur.a, left, right, prv.a, nxt.a, r);
+                }
+            }
+            prv = cur;
+            cur = nxt;
+        }
+    }
+}
+
+cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
+                   int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
+                   const hxc_launch_cfg *cfg, cudaStream_t s) {
+    if (ty <= 0 || tx <= 0) return cudaSuccess;
+    const int H = rows_per_warp > 0 ? rows_per_warp : 32;
+    const bool vec = (nx % 2 == 0) && (x0 % 2 == 0) && (tx % 2 == 0) &&
+                     (reinterpret_cast<uintptr_t>(src) % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(dst) % 16 == 0);
+    const int V = vec ? 2 : 1;
+    const int64_t nwork = ((tx + 32 * V - 1) / (32 * V)) * ((ty + H - 1) / H);
+    unsigned b = block_from(cfg, 256);
+    unsigned g = grid_from(cfg, std::min<int64_t>((nwork + b / 32 - 1) / (b / 32), (int64_t)sm_count() * 64));
+    if (vec)
+        k_heat2d<2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H);
+    else
+        k_heat2d<1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ tile snapshot/norm
+// Fixed reduction order: the tile's rows are cut into kNormBands bands
+// (band g = rows [g*ty/B, (g+1)*ty/B)); thread t of band g accumulates, in
+// increasing order, the squares of the band's elements whose row-major index
+// within the band is congruent to t mod 256 (acc = fma(v, v, acc)); the 256
+// partials are combined by a butterfly over lanes and a fixed tree over the
+// 8 warps; the last band to finish adds the band sums in order g = 0..B-1
+// and stores the square root.
+__global__ void __launch_bounds__(256) k_tile_norm(const double *__restrict__ src,
+                                                   double *__restrict__ snap, double *norms,
+                                                   double *partials, unsigned *counter,
+                                                   int64_t nx, int64_t y0, int64_t x0, int64_t ty,
+                                                   int64_t tx, int64_t index) {
+    const int g = blockIdx.x;
+    const int64_t r0 = (int64_t)g * ty / kNormBands, r1 = (int64_t)(g + 1) * ty / kNormBands;
+    const int64_t m = (r1 - r0) * tx;
+    double acc = 0.0;
+    int64_t i = r0 + threadIdx.x / tx, j = threadIdx.x % tx;  // element k = threadIdx.x
+    for (int64_t k = threadIdx.x; k < m; k += 256) {
+        const double v = __ldg(src + (y0 + i) * nx + x0 + j);
+        if (snap) snap[i * tx + j] = v;
+        acc = __fma_rn(v, v, acc);
+        j += 256;  // advance to element k + 256 of the band
+        if (j >= tx) {
+            i += j / tx;
+            j %= tx;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    __shared__ double ws[8];
+    __shared__ bool is_last;
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = __dadd_rn(__dadd_rn(__dadd_rn(ws[0], ws[1]), __dadd_rn(ws[2], ws[3])),
+                             __dadd_rn(__dadd_rn(ws[4], ws[5]), __dadd_rn(ws[6], ws[7])));
+        partials[g] = s;
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        is_last = (prev == kNormBands - 1);
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (int q = 0; q < kNormBands; q++) s = __dadd_rn(s, __ldcg(partials + q));
+        norms[index] = __dsqrt_rn(s);
+        *counter = 0u;  // leave the scratch ready for the next launch
+    }
+}
+
+cudaError_t tile_norm(const double *src, double *snap, double *norms, void *scratch,
+                      int64_t ny, int64_t nx, int64_t y0, int64_t x0, int64_t ty, int64_t tx,
+                      int64_t index, cudaStream_t s) {
+    (void)ny;
+    double *partials = static_cast<double *>(scratch);
+    unsigned *counter = reinterpret_cast<unsigned *>(partials + kNormBands);
+    k_tile_norm<<<kNormBands, 256, 0, s>>>(src, snap, norms, partials, counter, nx, y0, x0, ty,
+                                           tx, index);
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace hxc

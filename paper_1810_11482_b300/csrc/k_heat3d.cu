@@ -1,0 +1,191 @@
+// 3D 7-point FTCS, FP32, periodic, T (1..4) fused steps per launch.
+//
+// Canonical arithmetic (every variant, every T):
+//   s  = ((u[x-1] + u[x+1]) + (u[y-1] + u[y+1])) + (u[z-1] + u[z+1])
+//   t  = fma(-6, u, s);   u' = fma(r, t, u)            (FP32, round-to-nearest)
+// so T fused steps give the same bits as T single-step launches.
+//
+// Temporal blocking.  A CTA owns an x-y region of RX x RY = 64 x 32 columns
+// (its output tile plus a halo of T columns on every side) and streams it
+// along z.  Level t (the field after t steps) is kept per thread in
+// registers for three consecutive planes (z-1, z, z+1) of the 2 x 2 columns
+// the thread owns; x-neighbours come from the adjacent lanes by shuffles and
+// y-neighbours from a shared-memory copy of the level's middle plane.  In
+// every iteration a new level-0 plane is loaded and each level t < T
+// produces one plane of level t+1; the levels advance together (their
+// inputs are the registers and shared planes at the start of the
+// iteration), so level t runs 2t planes behind level 0.  Cells within
+// distance t of the region edge are wrong at level t and are never written:
+// only the central (RX-2T) x (RY-2T) columns of level T are stored.
+#include "kernels.cuh"
+
+namespace hxc {
+namespace k {
+
+namespace {
+constexpr int RX = 64, RY = 32, NT = 512;
+
+__device__ __forceinline__ float ftcs7(float u, float xm, float xp, float ym, float yp, float zm,
+                                       float zp, float r) {
+    float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+    float t = __fmaf_rn(-6.0f, u, s);
+    return __fmaf_rn(r, t, u);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+}  // namespace
+
+template <int T>
+__global__ void __launch_bounds__(NT, 1)
+    k_heat3d_tb(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
+                float r, int zchunk) {
+    constexpr int BX = RX - 2 * T, BY = RY - 2 * T;
+    __shared__ __align__(16) float S[T][RY][RX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles_x = (nx + BX - 1) / BX, tiles_y = (ny + BY - 1) / BY;
+    const int nchunks = (nz + zchunk - 1) / zchunk;
+    const int nblk = tiles_x * tiles_y * nchunks;
+    const int rx = 2 * lane, ry = 2 * warp;
+    // rows of the neighbouring warps (clamped inside the region: the clamped
+    // rows only feed cells that are never stored)
+    const int ryu = ry > 0 ? ry - 1 : 0, ryd = ry + 2 < RY ? ry + 2 : RY - 1;
+
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int tx = b % tiles_x, ty = (b / tiles_x) % tiles_y, ch = b / (tiles_x * tiles_y);
+        const int x0 = tx * BX - T, y0 = ty * BY - T;
+        const int z0 = ch * zchunk, z1 = min(nz, z0 + zchunk);
+        const int gx0 = wrapi(x0 + rx, nx), gx1 = wrapi(x0 + rx + 1, nx);
+        const int gy0 = wrapi(y0 + ry, ny), gy1 = wrapi(y0 + ry + 1, ny);
+        // output columns of this thread (inside the tile and the field)
+        const bool ox0 = rx >= T && rx < RX - T && x0 + rx < nx;
+        const bool ox1 = rx + 1 >= T && rx + 1 < RX - T && x0 + rx + 1 < nx;
+        const bool oy0 = ry >= T && ry < RY - T && y0 + ry < ny;
+        const bool oy1 = ry + 1 >= T && ry + 1 < RY - T && y0 + ry + 1 < ny;
+        const size_t o00 = (size_t)gy0 * nx + gx0, o01 = (size_t)gy0 * nx + gx1;
+        const size_t o10 = (size_t)gy1 * nx + gx0, o11 = (size_t)gy1 * nx + gx1;
+        const size_t plane = (size_t)ny * nx;
+
+        // level t planes: P = newest-2, M = newest-1, N = newest  (4 columns each)
+        float P[T][4], M[T][4], N[T][4];
+#pragma unroll
+        for (int t = 0; t < T; t++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) P[t][c] = M[t][c] = N[t][c] = 0.f;
+
+        const int iters = (z1 - z0) + 3 * T - 1;
+        // prefetch the first level-0 plane
+        float nxt[4];
+        {
+            const size_t zo = (size_t)wrapi(z0 - T, nz) * plane;
+            nxt[0] = __ldg(src + zo + o00);
+            nxt[1] = __ldg(src + zo + o01);
+            nxt[2] = __ldg(src + zo + o10);
+            nxt[3] = __ldg(src + zo + o11);
+        }
+        for (int i = 0; i < iters; i++) {
+            // level 0: shift in the loaded plane, prefetch the next one
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                P[0][c] = M[0][c];
+                M[0][c] = N[0][c];
+                N[0][c] = nxt[c];
+            }
+            if (i + 1 < iters) {
+                const size_t zo = (size_t)wrapi(z0 - T + i + 1, nz) * plane;
+                nxt[0] = __ldg(src + zo + o00);
+                nxt[1] = __ldg(src + zo + o01);
+                nxt[2] = __ldg(src + zo + o10);
+                nxt[3] = __ldg(src + zo + o11);
+            }
+            *reinterpret_cast<float2 *>(&S[0][ry][rx]) = make_float2(M[0][0], M[0][1]);
+            *reinterpret_cast<float2 *>(&S[0][ry + 1][rx]) = make_float2(M[0][2], M[0][3]);
+            __syncthreads();
+            // every level t produces level t+1 at the plane of M[t]
+            float V[T][4];
+#pragma unroll
+            for (int t = 0; t < T; t++) {
+                const float2 up = *reinterpret_cast<const float2 *>(&S[t][ryu][rx]);
+                const float2 dn = *reinterpret_cast<const float2 *>(&S[t][ryd][rx]);
+                const float l0 = __shfl_up_sync(0xffffffffu, M[t][1], 1);
+                const float r0 = __shfl_down_sync(0xffffffffu, M[t][0], 1);
+                const float l1 = __shfl_up_sync(0xffffffffu, M[t][3], 1);
+                const float r1 = __shfl_down_sync(0xffffffffu, M[t][2], 1);
+                V[t][0] = ftcs7(M[t][0], l0, M[t][1], up.x, M[t][2], P[t][0], N[t][0], r);
+                V[t][1] = ftcs7(M[t][1], M[t][0], r0, up.y, M[t][3], P[t][1], N[t][1], r);
+                V[t][2] = ftcs7(M[t][2], l1, M[t][3], M[t][0], dn.x, P[t][2], N[t][2], r);
+                V[t][3] = ftcs7(M[t][3], M[t][2], r1, M[t][1], dn.y, P[t][3], N[t][3], r);
+            }
+            __syncthreads();
+            // levels 1..T-1 shift in their new plane and publish the middle one
+#pragma unroll
+            for (int t = 1; t < T; t++) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    P[t][c] = M[t][c];
+                    M[t][c] = N[t][c];
+                    N[t][c] = V[t - 1][c];
+                }
+                *reinterpret_cast<float2 *>(&S[t][ry][rx]) = make_float2(M[t][0], M[t][1]);
+                *reinterpret_cast<float2 *>(&S[t][ry + 1][rx]) = make_float2(M[t][2], M[t][3]);
+            }
+            // level T: V[T-1] is the output plane z0 + i - 3T + 1
+            const int zout = z0 + i - 3 * T + 1;
+            if (zout >= z0 && zout < z1) {
+                float *d = dst + (size_t)zout * plane;
+                if (oy0 && ox0) d[o00] = V[T - 1][0];
+                if (oy0 && ox1) d[o01] = V[T - 1][1];
+                if (oy1 && ox0) d[o10] = V[T - 1][2];
+                if (oy1 && ox1) d[o11] = V[T - 1][3];
+            }
+        }
+        __syncthreads();  // the shared planes are reused by the next block item
+    }
+}
+
+int heat3d_blocks(int nz, int ny, int nx, int T, int zchunk) {
+    const int BX = RX - 2 * T, BY = RY - 2 * T;
+    return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + zchunk - 1) / zchunk);
+}
+
+// z chunk length: split z so that the CTA count fills whole waves of one
+// CTA per SM (each extra chunk re-reads 3T-1 planes).
+int heat3d_default_zchunk(int nz, int ny, int nx, int T) {
+    const int sms = sm_count();
+    int best = nz;
+    double best_eff = 0;
+    for (int nch = 1; nch <= 16 && nch <= nz; nch++) {
+        const int zc = (nz + nch - 1) / nch;
+        const int blocks = heat3d_blocks(nz, ny, nx, T, zc);
+        const int waves = (blocks + sms - 1) / sms;
+        const double fill = (double)blocks / ((double)waves * sms);
+        const double halo = (double)zc / (zc + 3 * T - 1);
+        const double eff = fill * halo;
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = zc;
+        }
+    }
+    return best;
+}
+
+cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r, int steps,
+                   int zchunk, const hxc_launch_cfg *cfg, cudaStream_t s) {
+    if (steps < 1 || steps > 4) return cudaErrorInvalidValue;
+    if (zchunk <= 0) zchunk = heat3d_default_zchunk(nz, ny, nx, steps);
+    const int blocks = heat3d_blocks(nz, ny, nx, steps, zchunk);
+    unsigned g = cfg ? cfg->grid[0] * cfg->grid[1] * cfg->grid[2] : (unsigned)blocks;
+    if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != NT) return cudaErrorInvalidValue;
+    switch (steps) {
+        case 1: k_heat3d_tb<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        case 2: k_heat3d_tb<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        case 3: k_heat3d_tb<3><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        case 4: k_heat3d_tb<4><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace hxc

@@ -1,0 +1,57 @@
+// Launchers of the sm_103a kernels.  Arguments are raw device pointers;
+// the C ABI layer validates sizes and handles before calling these.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "hxc.h"
+
+namespace hxc {
+namespace k {
+
+// Number of row bands of the tile-norm reduction; fixed so that the
+// reduction order (and therefore every bit of the result) does not depend
+// on how tiles are grouped into launches.
+constexpr int kNormBands = 64;
+// Scratch of one tile-norm launch: kNormBands partial sums + a counter.
+constexpr size_t kNormScratchBytes = kNormBands * sizeof(double) + 16;
+
+int sm_count();
+
+cudaError_t sum_u32(const uint32_t *in, unsigned long long *result, int64_t n,
+                    const hxc_launch_cfg *cfg, cudaStream_t s);
+cudaError_t prk(const double *in, double *out, int64_t n, const hxc_launch_cfg *cfg,
+                cudaStream_t s);
+cudaError_t partition(double *out, int64_t n, int64_t offset, const hxc_launch_cfg *cfg,
+                      cudaStream_t s);
+
+// dst[lo, lo+count) <- `steps` periodic FTCS steps of src (period n).
+cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
+                   double r, int steps, const hxc_launch_cfg *cfg, cudaStream_t s);
+// Largest `steps` a single temporally blocked 1D launch accepts.
+constexpr int kHeat1dMaxSteps = 1024;
+
+// One 2D FTCS step of the tile [y0, y0+ty) x [x0, x0+tx); rows_per_warp <= 0
+// picks the default.
+cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
+                   int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
+                   const hxc_launch_cfg *cfg, cudaStream_t s);
+
+// Snapshot + L2 norm of a tile: snap (optional, compact ty x tx) <- tile of
+// src; norms[index] <- sqrt(sum u^2) in a fixed order.  scratch holds
+// kNormScratchBytes, zero on first use, returned to zero by the kernel;
+// launches that may run concurrently need distinct scratch.
+cudaError_t tile_norm(const double *src, double *snap, double *norms, void *scratch,
+                      int64_t ny, int64_t nx, int64_t y0, int64_t x0, int64_t ty, int64_t tx,
+                      int64_t index, cudaStream_t s);
+
+// 3D FTCS, FP32, periodic: `steps` (1..4) fused steps per launch.  zchunk
+// <= 0 picks the z-chunk length that fills whole waves.
+cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r, int steps,
+                   int zchunk, const hxc_launch_cfg *cfg, cudaStream_t s);
+int heat3d_default_zchunk(int nz, int ny, int nx, int T);
+
+}  // namespace k
+}  // namespace hxc

@@ -1,0 +1,192 @@
+"""CPU checks of the C-ABI library: it loads, exports every function that
+include/hxc.h declares, its structs match the binding's layouts, and the
+host side of the future layer (promises, then, when_all, wait_all, error
+propagation, timeouts) behaves as specified without touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+import threading
+import time
+
+import pytest
+
+from paper_1810_11482_b300 import hxc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def _declared_functions():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        # declarations: "<return type> hxc_name(" at the start of a line
+        for m in re.finditer(r"^\s*(?!typedef)(?:const\s+)?\w+\s*\**\s*(hxc_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1810_11482_b300 import build
+    build.build()
+    return hxc.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = _declared_functions()
+    assert len(names) > 40
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding covers the same set
+    unbound = [n for n in names if n not in hxc._SIGS]
+    assert not unbound, unbound
+
+
+def test_struct_layouts_match_header(L):
+    structs = ["hxc_launch_cfg", "hxc_sum_args", "hxc_prk_args", "hxc_heat1d_args",
+               "hxc_heat2d_args", "hxc_tile_norm2_args", "hxc_partition_args", "hxc_run_stats",
+               "hxc_heat2d_cfg"]
+    structs += [s for s in getattr(hxc, "EXTRA_STRUCTS", [])]
+    prog = "#include <stdio.h>\n#include \"hxc.h\"\nint main(void){\n"
+    for s in structs:
+        prog += 'printf("%%s %%zu\\n", "%s", sizeof(%s));\n' % (s, s)
+    prog += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe], text=True)
+    sizes = dict(line.split() for line in out.strip().splitlines())
+    for s in structs:
+        assert int(sizes[s]) == ctypes.sizeof(getattr(hxc, s)), s
+
+
+def test_status_strings_and_version(L):
+    assert L.hxc_abi_version() == 1
+    assert L.hxc_status_string(hxc.HXC_E_TIMEOUT) == b"timeout"
+    assert L.hxc_status_string(hxc.HXC_E_DEP_FAILED) == b"dependency failed"
+
+
+def test_invalid_handles_rejected(L):
+    bogus = ctypes.c_void_p(0)
+    assert L.hxc_future_wait(bogus, 0) == hxc.HXC_E_INVALID
+    assert L.hxc_buffer_release(bogus) == hxc.HXC_E_INVALID
+    r = ctypes.c_int()
+    assert L.hxc_future_is_ready(bogus, ctypes.byref(r)) == hxc.HXC_E_INVALID
+    assert L.hxc_future_then(bogus, hxc.HOST_FN(lambda u: 0), None, None) == hxc.HXC_E_INVALID
+
+
+def test_promise_then_chain_runs_in_order(L):
+    log = []
+    p = hxc.promise()
+    a = p.then(lambda: log.append("a"))
+    b = a.then(lambda: log.append("b"))
+    time.sleep(0.05)
+    assert log == [] and not b.is_ready()
+    hxc.promise_set(p)
+    b.get(timeout_ns=5_000_000_000)
+    assert log == ["a", "b"]
+
+
+def test_continuation_runs_on_worker_thread(L):
+    main = threading.get_ident()
+    seen = []
+    f = hxc.make_ready_future().then(lambda: seen.append(threading.get_ident()))
+    f.get(5_000_000_000)
+    assert seen and seen[0] != main
+
+
+def test_failure_propagates_and_skips_continuations(L):
+    ran = []
+    p = hxc.promise()
+    c = p.then(lambda: ran.append(1))
+    d = c.then(lambda: ran.append(2))
+    hxc.promise_set(p, hxc.HXC_E_CUDA)  # inject a host-side failure
+    assert p.wait(5_000_000_000) == hxc.HXC_E_CUDA
+    assert c.wait(5_000_000_000) == hxc.HXC_E_DEP_FAILED
+    assert d.wait(5_000_000_000) == hxc.HXC_E_DEP_FAILED
+    assert ran == []
+
+
+def test_callback_error_becomes_callback_status(L):
+    def boom():
+        raise ValueError("x")
+    f = hxc.make_ready_future().then(boom)
+    assert f.wait(5_000_000_000) == hxc.HXC_E_CALLBACK
+    g = f.then(lambda: None)
+    assert g.wait(5_000_000_000) == hxc.HXC_E_DEP_FAILED
+
+
+def test_when_all_joins_and_propagates(L):
+    ps = [hxc.promise() for _ in range(5)]
+    j = hxc.when_all(ps)
+    for p in ps[:4]:
+        hxc.promise_set(p)
+    assert j.wait(20_000_000) == hxc.HXC_E_TIMEOUT  # one input still open
+    hxc.promise_set(ps[4])
+    assert j.wait(5_000_000_000) == hxc.HXC_OK
+    qs = [hxc.promise() for _ in range(3)]
+    k = hxc.when_all(qs)
+    hxc.promise_set(qs[0])
+    hxc.promise_set(qs[1], hxc.HXC_E_NOMEM)
+    hxc.promise_set(qs[2])
+    assert k.wait(5_000_000_000) == hxc.HXC_E_DEP_FAILED
+    assert hxc.when_all([]).wait(0) == hxc.HXC_OK
+
+
+def test_wait_timeout_then_success(L):
+    p = hxc.promise()
+    t0 = time.time()
+    assert p.wait(50_000_000) == hxc.HXC_E_TIMEOUT
+    assert time.time() - t0 >= 0.04
+    assert b"timeout" in L.hxc_last_error()
+    threading.Timer(0.05, lambda: hxc.promise_set(p)).start()
+    assert p.wait(5_000_000_000) == hxc.HXC_OK
+
+
+def test_wait_all_reports_first_failure(L):
+    fs = [hxc.make_ready_future(), hxc.make_ready_future(hxc.HXC_E_CALLBACK),
+          hxc.make_ready_future(hxc.HXC_E_NOMEM)]
+    assert hxc.wait_all(fs, 1_000_000_000) == hxc.HXC_E_CALLBACK
+    assert hxc.wait_all([hxc.promise()], 10_000_000) == hxc.HXC_E_TIMEOUT
+
+
+def test_promise_set_twice_rejected(L):
+    p = hxc.promise()
+    hxc.promise_set(p)
+    with pytest.raises(hxc.HxcError):
+        hxc.promise_set(p)
+
+
+def test_many_concurrent_continuations(L):
+    n = 2000
+    count = []
+    lock = threading.Lock()
+
+    def inc():
+        with lock:
+            count.append(1)
+    root = hxc.promise()
+    leaves = [root.then(inc) for _ in range(n)]
+    hxc.promise_set(root)
+    assert hxc.wait_all(leaves, 10_000_000_000) == hxc.HXC_OK
+    assert len(count) == n
+
+
+def test_get_all_devices_without_gpu(L):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    assert hxc.get_all_devices(2, 0) == []
+    n = ctypes.c_int(-1)
+    assert L.hxc_get_all_devices(2, 0, None, 0, ctypes.byref(n)) == hxc.HXC_E_NODEV
+    assert n.value == 0

@@ -1,0 +1,283 @@
+"""GPU parity of the 1D/2D path against the FP64 oracle, through the C ABI.
+
+Tolerance: norm-wise relative error max|u_gpu - u_oracle| / max|u_oracle|
+<= 1e-12.  The oracle rounds every operation separately (no FMA) while the
+kernels use fused multiply-adds, so the two differ by rounding only: a few
+ulps per step, well inside 1e-12 for the step counts used here.
+Schedules of the GPU path (partition counts, tile grids, plain / graph /
+fused launches) must agree bit for bit."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_11482_b300 import hxc, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dev():
+    devs = hxc.get_all_devices(2, 0)
+    assert devs, "no CUDA device"
+    return devs[0]
+
+
+def upload(dev, a):
+    a = np.ascontiguousarray(a)
+    b = dev.buffer(a.nbytes)
+    b.write(a).get()
+    return b
+
+
+def download(buf, shape, dtype=np.float64):
+    out = np.empty(shape, dtype=dtype)
+    buf.read_sync(out)
+    return out
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ------------------------------------------------------------- Listing 2
+
+def test_listing2_sum_workflow(dev):
+    """Listing 2: buffers, async writes, wait_all, sum kernel with grid 1x1x1
+    and block 32x1x1, synchronous read of the result."""
+    n = 1000
+    inp = np.ones(n, dtype=np.uint32)
+    res = np.zeros(1, dtype=np.uint64)
+    b_in, b_res = dev.buffer(n * 4), dev.buffer(8)
+    futs = [b_in.write(inp), b_res.write(res)]
+    assert hxc.wait_all(futs) == hxc.HXC_OK
+    cfg = hxc.hxc_launch_cfg((1, 1, 1), (32, 1, 1))
+    a = hxc.hxc_sum_args(b_in.h, b_res.h, n)
+    dev.launch(hxc.HXC_K_SUM_U32, a, cfg=cfg).get()
+    out = np.zeros(1, dtype=np.uint64)
+    b_res.read_sync(out)
+    assert int(out[0]) == 1000 == oracle.sum_u32(inp)
+    # a larger ragged input, default launch shape
+    x = (synth.splitmix64(9, 100003) >> np.uint64(40)).astype(np.uint32)
+    b_x, b_r = upload(dev, x), upload(dev, np.zeros(1, dtype=np.uint64))
+    dev.launch(hxc.HXC_K_SUM_U32, hxc.hxc_sum_args(b_x.h, b_r.h, x.size)).get()
+    assert int(download(b_r, 1, np.uint64)[0]) == oracle.sum_u32(x)
+
+
+def test_prk_stencil_bitexact(dev):
+    x = synth.uniform(10, 4099, lo=-1, hi=1)
+    bi, bo = upload(dev, x), dev.buffer(x.nbytes)
+    dev.launch(hxc.HXC_K_PRK_STENCIL, hxc.hxc_prk_args(bi.h, bo.h, x.size)).get()
+    assert np.array_equal(download(bo, x.size), oracle.prk_stencil(x))
+
+
+def test_partition_kernel_is_one(dev):
+    """Sec. 5.1.2: sqrt(sin^2 i + cos^2 i) = 1 within CUDA's sin/cos/sqrt error bounds."""
+    n = 1 << 20
+    b = dev.buffer(n * 8)
+    dev.launch(hxc.HXC_K_PARTITION, hxc.hxc_partition_args(b.h, n, 12345)).get()
+    out = download(b, n)
+    assert np.max(np.abs(out - 1.0)) <= 8 * np.finfo(np.float64).eps
+
+
+# ------------------------------------------------------------------ 1D
+
+def run1d(dev, u0, parts, r, steps, mode="plain", spl=0):
+    u, t = upload(dev, u0), dev.buffer(u0.nbytes)
+    f, st = hxc.heat1d_run(dev, u, t, u0.size, parts, r, steps, mode, spl)
+    f.get()
+    return download(u, u0.size), st
+
+
+@pytest.mark.parametrize("n,parts", [(1000, 3), (1023, 7), (17, 5), (4096, 1)])
+@pytest.mark.parametrize("r", [0.25, 0.2])
+def test_heat1d_vs_oracle_small(dev, n, parts, r):
+    u0 = synth.heat1d_input(n, seed=100 + n)
+    for steps in (1, 2, 37):
+        want = oracle.heat1d(u0, r, steps)
+        for mode, spl in (("plain", 0), ("fused", 0), ("fused", 5), ("graph", 0)):
+            got, _ = run1d(dev, u0, parts, r, steps, mode, spl)
+            assert relerr(got, want) <= TOL, (mode, spl, steps)
+
+
+def test_heat1d_bitexact_across_schedules(dev):
+    n, steps, r = 1 << 16, 37, 0.25
+    u0 = synth.heat1d_input(n, seed=101)
+    ref, _ = run1d(dev, u0, 1, r, steps, "plain")
+    for parts in (2, 4, 8, 16):
+        for mode, spl in (("plain", 0), ("graph", 0), ("fused", 0), ("fused", 1), ("fused", 7)):
+            got, _ = run1d(dev, u0, parts, r, steps, mode, spl)
+            assert np.array_equal(got, ref), (parts, mode, spl)
+
+
+def test_heat1d_full_config_vs_oracle(dev):
+    """2^20 points, 8 partitions, r = 1/4, 100 steps, every mode."""
+    n, r, steps = 1 << 20, 0.25, 100
+    u0 = synth.heat1d_input(n, seed=1)
+    want = oracle.heat1d(u0, r, steps)
+    outs = []
+    for mode in ("plain", "graph", "fused"):
+        got, st = run1d(dev, u0, 8, r, steps, mode)
+        assert relerr(got, want) <= TOL, mode
+        outs.append(got)
+    assert all(np.array_equal(o, outs[0]) for o in outs)
+
+
+def test_heat1d_fourier_mode_exact_decay(dev):
+    n, r, steps = 1 << 20, 0.25, 100
+    j = np.arange(n)
+    u0 = np.sin(2 * np.pi * 3 * j / n)
+    g = 1.0 - 2.0 * r * (1.0 - math.cos(2 * math.pi * 3 / n))
+    got, _ = run1d(dev, u0, 8, r, steps, "fused")
+    assert np.max(np.abs(got - g ** steps * u0)) <= 16 * steps * np.finfo(float).eps
+    # Nyquist mode vanishes exactly after one step at r = 1/4
+    got, _ = run1d(dev, np.where(j % 2 == 0, 1.0, -1.0), 8, 0.25, 1, "plain")
+    assert np.all(got == 0.0)
+
+
+def test_heat1d_zero_steps_and_args(dev):
+    u0 = synth.heat1d_input(64, seed=3)
+    got, _ = run1d(dev, u0, 4, 0.25, 0)
+    assert np.array_equal(got, u0)
+    u, t = upload(dev, u0), dev.buffer(u0.nbytes)
+    with pytest.raises(hxc.HxcError):
+        hxc.heat1d_run(dev, u, u, 64, 4, 0.25, 3)  # aliasing buffers rejected
+    with pytest.raises(hxc.HxcError):
+        hxc.heat1d_run(dev, u, t, 64, 65, 0.25, 3)  # more partitions than points
+
+
+# ------------------------------------------------------------------ 2D
+
+def run2d(dev, u0, tiles, r, steps, mode="plain", every=0):
+    ny, nx = u0.shape
+    u, t = upload(dev, u0), dev.buffer(u0.nbytes)
+    nsnap = steps // every if every else 0
+    T = tiles[0] * tiles[1]
+    hn = np.full(max(1, nsnap * T), np.nan)
+    gn = np.full(max(1, nsnap * T), np.nan)
+    cfg = hxc.heat2d_cfg(ny, nx, tiles[0], tiles[1], r, steps, every, mode,
+                         hn if nsnap else None, gn if nsnap else None)
+    f, st = hxc.heat2d_run(dev, u, t, cfg)
+    f.get()
+    return download(u, (ny, nx)), hn[:nsnap * T].reshape(nsnap, T), gn[:nsnap * T].reshape(nsnap, T), st
+
+
+@pytest.mark.parametrize("shape,tiles", [((100, 130), (3, 4)), ((77, 93), (2, 5)),
+                                         ((64, 64), (1, 1)), ((33, 200), (4, 1))])
+def test_heat2d_vs_oracle_small(dev, shape, tiles):
+    u0 = synth.bumps2d(*shape, seed=200 + shape[0], nbumps=5, sigma=0.1)
+    for r in (0.2, 0.25):
+        for steps in (1, 2, 21):
+            want = oracle.heat2d(u0, r, steps)
+            for mode in ("plain", "graph", "fused"):
+                got, _, _, _ = run2d(dev, u0, tiles, r, steps, mode)
+                assert relerr(got, want) <= TOL, (mode, r, steps)
+
+
+def test_heat2d_bitexact_across_tilings_and_modes(dev):
+    u0 = synth.bumps2d(512, 384, seed=210, nbumps=8, sigma=0.05)
+    ref, _, _, _ = run2d(dev, u0, (1, 1), 0.2, 25, "plain")
+    for tiles in ((2, 2), (8, 8), (3, 5), (7, 1)):
+        for mode in ("plain", "graph", "fused"):
+            got, _, _, _ = run2d(dev, u0, tiles, 0.2, 25, mode)
+            assert np.array_equal(got, ref), (tiles, mode)
+    # mirror symmetry is exact: the flipped input gives the flipped output
+    got, _, _, _ = run2d(dev, u0[::-1, ::-1].copy(), (2, 2), 0.2, 25, "fused")
+    assert np.array_equal(got, ref[::-1, ::-1])
+
+
+def test_heat2d_snapshot_norms(dev):
+    """Host norms (then-continuations on device->host snapshots) and device
+    norms (fixed-order reduction) against the oracle's tile norms."""
+    u0 = synth.bumps2d(256, 320, seed=220, nbumps=6, sigma=0.05)
+    tiles, every, steps, r = (4, 5), 7, 30, 0.2
+    for mode in ("plain", "graph", "fused"):
+        _, hn, gn, st = run2d(dev, u0, tiles, r, steps, mode, every)
+        assert st.host_tasks == (steps // every) * 20
+        for k in range(steps // every):
+            state = oracle.heat2d(u0, r, (k + 1) * every)
+            want = oracle.tile_norms(state[:, :], 64, 64).ravel()
+            assert np.max(np.abs(hn[k] - want) / want) <= 1e-12, (mode, k)
+            assert np.max(np.abs(gn[k] - want) / want) <= 1e-12, (mode, k)
+            assert np.max(np.abs(gn[k] - hn[k]) / hn[k]) <= 1e-14
+    # device norms are bit-identical across modes (fixed reduction order)
+    _, _, g1, _ = run2d(dev, u0, tiles, r, steps, "plain", every)
+    _, _, g2, _ = run2d(dev, u0, tiles, r, steps, "graph", every)
+    _, _, g3, _ = run2d(dev, u0, tiles, r, steps, "fused", every)
+    assert np.array_equal(g1, g2) and np.array_equal(g1, g3)
+
+
+def test_heat2d_full_config(dev):
+    """8192^2, 64 tiles of 1024^2, r = 0.2, 1000 steps, snapshots every 100
+    steps: every mode bit-identical; a corner window checked against the
+    oracle (the dependence cone of a cell after 1000 steps is 1000 cells
+    wide, so cells 1000 away from the window's cut edges are exact); device
+    norms against host norms; the last snapshot's norms against norms of the
+    downloaded final field."""
+    n, steps, r, every = 8192, 1000, 0.2, 100
+    u0 = synth.bumps2d(n, n, seed=2)
+    outs = {}
+    for mode in ("plain", "graph", "fused"):
+        got, hn, gn, st = run2d(dev, u0, (8, 8), r, steps, mode, every)
+        outs[mode] = got
+        assert np.max(np.abs(gn - hn) / np.maximum(hn, 1e-300)) <= 1e-14
+    assert np.array_equal(outs["plain"], outs["graph"])
+    assert np.array_equal(outs["plain"], outs["fused"])
+    got = outs["plain"]
+    scale = np.max(np.abs(got))
+    w = oracle.heat2d_window(u0, n - 1300, n - 1300, 1300, 1300, r, steps)
+    assert np.max(np.abs(got[n - 300:, n - 300:] - w[1000:, 1000:])) <= TOL * scale
+    fin = np.array([np.sqrt(np.sum(got[i * 1024:(i + 1) * 1024, j * 1024:(j + 1) * 1024]
+                                   .astype(np.longdouble) ** 2))
+                    for i in range(8) for j in range(8)], dtype=np.float64)
+    assert np.max(np.abs(hn[-1] - fin) / fin) <= 1e-13
+
+
+def test_heat2d_full_size_window_at_peak(dev):
+    """Full 8192^2 field, 150 steps, oracle window centred on the largest
+    initial value (where the solution is significant)."""
+    n, steps, r = 8192, 150, 0.2
+    u0 = synth.bumps2d(n, n, seed=2)
+    got, _, _, _ = run2d(dev, u0, (8, 8), r, steps, "plain")
+    ci, cj = np.unravel_index(np.argmax(u0), u0.shape)
+    half = steps + 64
+    y0, x0 = max(0, ci - half), max(0, cj - half)
+    wy, wx = min(n, ci + half) - y0, min(n, cj + half) - x0
+    w = oracle.heat2d_window(u0, y0, x0, wy, wx, r, steps)
+    ey0 = 0 if y0 == 0 else steps
+    ex0 = 0 if x0 == 0 else steps
+    ey1 = wy if y0 + wy == n else wy - steps
+    ex1 = wx if x0 + wx == n else wx - steps
+    exact = w[ey0:ey1, ex0:ex1]
+    mine = got[y0 + ey0:y0 + ey1, x0 + ex0:x0 + ex1]
+    assert exact.size > 0
+    assert np.max(np.abs(mine - exact)) <= TOL * np.max(np.abs(got))
+
+
+def test_heat2d_sine_mode_full_size(dev):
+    """A Dirichlet sine mode on the full 8192^2 grid decays by exactly
+    g^n, g = 1 - 4 r [sin^2(p pi h/2) + sin^2(q pi h/2)], up to rounding."""
+    n, r, steps, p, q = 8192, 0.2, 200, 3, 5
+    h = 1.0 / (n + 1)
+    x = (np.arange(n) + 1) * h
+    u0 = np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x))
+    g = 1.0 - 4.0 * r * (math.sin(p * math.pi * h / 2) ** 2 + math.sin(q * math.pi * h / 2) ** 2)
+    got, _, _, _ = run2d(dev, u0, (8, 8), r, steps, "fused")
+    assert np.max(np.abs(got - g ** steps * u0)) <= 64 * steps * np.finfo(float).eps
+
+
+def test_heat2d_host_entry_point(dev):
+    """hxc_heat2d_run_host: field in pinned host memory, per-tile copies."""
+    ny, nx = 1024, 768
+    u0 = synth.bumps2d(ny, nx, seed=230, nbumps=6, sigma=0.05)
+    hu = hxc.host_empty((ny, nx))
+    hu[:] = u0
+    out = hxc.host_empty((ny, nx))
+    hn = np.zeros(2 * 12)
+    cfg = hxc.heat2d_cfg(ny, nx, 4, 3, 0.2, 40, 20, "plain", hn, None)
+    st = hxc.heat2d_run_host(dev, hu.ctypes.data, out.ctypes.data, cfg)
+    want = oracle.heat2d(u0, 0.2, 40)
+    assert relerr(np.array(out), want) <= TOL
+    assert st.h2d_bytes == u0.nbytes and st.d2h_bytes >= u0.nbytes
