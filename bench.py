@@ -284,6 +284,10 @@ def ours(args, world, rank, local, pg):
                "h2d_bytes_per_step": int(st.h2d_bytes), "d2h_bytes_per_step": int(st.d2h_bytes),
                "steps": k}
 
+    sec = None
+    if not args.quick and not args.no_secondary:
+        sec = secondary(dev, timer, peaks)
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -293,8 +297,109 @@ def ours(args, world, rank, local, pg):
                    "mode": best_mode, "parallelism": "replicas x%d" % world,
                    "l2": "field 2x512 MiB > 126 MB L2 (no flush needed)"},
         "roofline": roof, "gpu_launches": int(allsum(pg, n_launch)), "modes": modes,
-        "clocks": clk, "e2e": e2e,
+        "clocks": clk, "e2e": e2e, "secondary": sec,
     }
+    return out
+
+
+def secondary(dev, timer, peaks):
+    """The other workloads of the path, each in every launch mode on the same
+    GPU: updates/s per mode and the speed-up over the plain per-partition
+    (or per-problem / unfused) launch path."""
+    from paper_1810_11482_b300 import hxc, synth
+
+    def timed_run(fn, reps=1, warm=1):
+        for _ in range(warm):
+            f = fn(None)
+            f.get()
+        start = timer.start()
+        f = start
+        for _ in range(reps):
+            f = fn(f)
+        return timer.stop(f) / reps
+
+    def speedups(res, modes=("plain", "graph", "fused")):
+        for m in modes:
+            res[m]["speedup_vs_plain"] = res["plain"]["ms"] / res[m]["ms"]
+
+    out = {}
+    # 1D periodic, 2^20 points in 8 partitions, r = 1/4, 100 steps
+    n, parts, st1 = 1 << 20, 8, 100
+    u0 = synth.heat1d_input(n, seed=1)
+    u, t = dev.buffer(n * 8), dev.buffer(n * 8)
+    u.write(u0).get()
+    res = {}
+    for mode in ("plain", "graph", "fused"):
+        ms = timed_run(lambda d, m=mode: hxc.heat1d_run(dev, u, t, n, parts, 0.25, st1, m, 0,
+                                                         deps=[d] if d else ())[0], reps=5, warm=2)
+        res[mode] = {"ms": ms, "updates_per_s": n * st1 / (ms / 1e3)}
+    speedups(res)
+    out["heat1d_2^20_8parts_100steps_f64"] = res
+
+    # 3D periodic FP32 512^3, r = 0.15, 200 steps, 4 steps per launch
+    n3, st3 = 512, 200
+    u3 = synth.heat3d_input(n3, seed=3)
+    a, b = dev.buffer(u3.nbytes), dev.buffer(u3.nbytes)
+    a.write(u3).get()
+    res = {}
+    for mode, spl in (("plain", 1), ("graph", 4), ("fused", 4)):
+        ms = timed_run(lambda d, m=mode, k=spl: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, st3, m, k,
+                                                                deps=[d] if d else ())[0])
+        res[mode] = {"ms": ms, "updates_per_s": n3 ** 3 * st3 / (ms / 1e3), "steps_per_launch": spl}
+    speedups(res)
+    # per-launch HBM roofline of the 4-step kernel (algorithmic: read + write once)
+    launch_ms = res["fused"]["ms"] / (st3 / 4)
+    gbs = 2 * u3.nbytes / (launch_ms / 1e3) / 1e9
+    res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": gbs / peaks["hbm_gbs"], "ms_per_launch": launch_ms,
+                       "effective_gbs_1step_equiv": 2 * u3.nbytes * st3 / (res["fused"]["ms"] / 1e3) / 1e9}
+    out["heat3d_512^3_200steps_f32"] = res
+    del u3
+
+    # batch: 4096 variable-diffusivity problems, 50 steps
+    sides, offs, kap, ub, cs = synth.batch_input(nprob=4096, seed=4)
+    total = ub.size
+    bu, bk = dev.buffer(total * 8), dev.buffer(total * 8)
+    bk.write(kap).get()
+    res, outs = {}, {}
+    for mode in ("plain", "graph", "fused"):
+        bu.write(ub).get()
+        ms = timed_run(lambda d, m=mode: hxc.varcoef_batch_run(dev, bu, bk, sides, cs, 50, m,
+                                                                deps=[d] if d else ())[0], warm=1)
+        chk = np.empty(1 << 16)
+        bu.read_sync(chk, off=(total // 2) * 8)
+        outs[mode] = chk
+        res[mode] = {"ms": ms, "updates_per_s": total * 50 / (ms / 1e3)}
+    speedups(res)
+    res["bitwise_equal_modes"] = bool(all(np.array_equal(outs["plain"], outs[m]) for m in outs))
+    res["points"] = int(total)
+    out["batch_4096_problems_50steps_f64"] = res
+    del kap, ub
+
+    # adjoint: 2048^2, 500 steps, sqrt(n) checkpointing
+    n2, st4, c = 2048, 500, 0.15
+    kref, kap, u0, _ = synth.adjoint_input(n2)
+    b0, bkr, bkk = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    b0.write(u0).get()
+    bkr.write(kref).get()
+    bkk.write(kap).get()
+    tgt, uT, lam, lb = (dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes),
+                        dev.buffer(8))
+    hxc.varcoef_forward_run(dev, b0, bkr, n2, n2, c, st4, tgt)[0].get()
+    hxc.varcoef_forward_run(dev, b0, bkk, n2, n2, c, st4, uT)[0].get()
+    hxc.sqerr_seed(dev, uT, tgt, lam, lb, n2 * n2).get()
+    gk, gu = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    res = {}
+    ms = timed_run(lambda d: hxc.varcoef_forward_run(dev, b0, bkk, n2, n2, c, st4, uT,
+                                                     deps=[d] if d else ())[0])
+    res["forward"] = {"ms": ms, "updates_per_s": n2 * n2 * st4 / (ms / 1e3)}
+    for mode in ("plain", "graph", "fused"):
+        ms = timed_run(lambda d, m=mode: hxc.varcoef_adjoint_run(dev, b0, bkk, lam, n2, n2, c, st4, gk, gu,
+                                                                  None, 0, m, deps=[d] if d else ())[0])
+        res[mode] = {"ms": ms, "gradient_updates_per_s": n2 * n2 * st4 / (ms / 1e3)}
+    speedups(res)
+    res["gradient_over_forward_time"] = res["fused"]["ms"] / res["forward"]["ms"]
+    out["adjoint_2048^2_500steps_f64"] = res
     return out
 
 
@@ -346,6 +451,8 @@ def main():
     ap.add_argument("--mode", default="fused", choices=["plain", "graph", "fused"])
     ap.add_argument("--quick", action="store_true", help="skip mode comparison and e2e")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 1D/3D/batch/adjoint comparisons")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

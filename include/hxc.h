@@ -359,6 +359,56 @@ hxc_status hxc_heat3d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, int64_t 
                           const hxc_future *deps, int ndeps, hxc_future *out,
                           hxc_run_stats *stats);
 
+/* A batch of independent variable-diffusivity problems (Dirichlet-zero,
+ * flux form with arithmetic face mean), `nprob` square problems of side
+ * sides[p] packed back to back in u and kappa (problem p starts at element
+ * sum_{q<p} sides[q]^2), each with its own c[p] = dt/h^2.  u holds the initial
+ * fields and receives the results after `steps` steps.  sides and c are host
+ * arrays read during the call.  PLAIN launches one kernel per problem and
+ * step (plus one coefficient kernel per problem), GRAPH replays a captured
+ * sequence of batched per-step launches, FUSED runs one persistent launch in
+ * which every CTA takes whole problems (largest first) from a queue.  All
+ * modes give bit-identical results.  Uses device scratch (a second field,
+ * three coefficient arrays, the problem list and a work counter) shared by
+ * all batch runs on the device: a run must depend on the future of any
+ * earlier batch run it could otherwise overlap with. */
+hxc_status hxc_varcoef_batch_run(hxc_device dev, hxc_buffer u, hxc_buffer kappa,
+                                 const int64_t *sides, const double *c, int64_t nprob, int steps,
+                                 hxc_mode mode, const hxc_future *deps, int ndeps,
+                                 hxc_future *out, hxc_run_stats *stats);
+
+/* Squared error and adjoint seed: loss[0] = sum_i (u_i - t_i)^2 (fixed
+ * reduction order) and, if lam is not NULL, lam_i = 2 (u_i - t_i).  u, t and
+ * lam hold n doubles, loss one double. */
+hxc_status hxc_sqerr_seed(hxc_device dev, hxc_buffer u, hxc_buffer t, hxc_buffer lam,
+                          hxc_buffer loss, int64_t n, int slot, const hxc_future *deps,
+                          int ndeps, hxc_future *out);
+
+/* Reverse-mode gradient of a scalar loss of u^T through `steps`
+ * variable-diffusivity steps on one ny x nx problem: given u0, kappa and
+ * lamT = dL/du^T, computes gk = dL/dkappa and gu0 = dL/du0 (= lambda^0),
+ * and the final state into uT if uT is not NULL.  The forward states are
+ * kept only every `every` steps (0: every = ceil(sqrt(steps))) and each
+ * segment is recomputed from its checkpoint before its adjoint steps;
+ * every = 1 stores every state.  c is fixed (not differentiated).  FUSED
+ * fuses the adjoint step with the kappa-gradient accumulation, PLAIN
+ * launches them separately, GRAPH replays the captured fused sequence.  The
+ * results are bit-identical for every mode and every `every`.  Device
+ * scratch (coefficients, checkpoints, the segment store, work and adjoint
+ * fields) is shared by the adjoint runs of a device: order overlapping runs
+ * with futures. */
+hxc_status hxc_varcoef_adjoint_run(hxc_device dev, hxc_buffer u0, hxc_buffer kappa,
+                                   hxc_buffer lamT, int64_t ny, int64_t nx, double c, int steps,
+                                   int every, hxc_mode mode, hxc_buffer gk, hxc_buffer gu0,
+                                   hxc_buffer uT, const hxc_future *deps, int ndeps,
+                                   hxc_future *out, hxc_run_stats *stats);
+/* Forward only: `steps` variable-diffusivity steps of u0 into uT (one
+ * problem; coefficients computed once; uT must not alias u0 or kappa). */
+hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kappa, int64_t ny,
+                                   int64_t nx, double c, int steps, hxc_buffer uT,
+                                   const hxc_future *deps, int ndeps, hxc_future *out,
+                                   hxc_run_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -734,6 +734,45 @@ hxc_status hxc_launch(hxc_device dh, hxc_kernel_id id, const void *args, size_t 
             };
             break;
         }
+        case HXC_K_VARCOEF2D: {
+            ARGS(hxc_varcoef2d_args);
+            if (a.ny <= 0 || a.nx <= 0 || !cfg_ok(pc, 32, 1024)) goto bad;
+            size_t bytes = (size_t)a.ny * a.nx * 8;
+            BUF(src, a.src, bytes, "varcoef2d.src");
+            BUF(dst, a.dst, bytes, "varcoef2d.dst");
+            BUF(kap, a.kappa, bytes, "varcoef2d.kappa");
+            if (src->ptr == dst->ptr || kap->ptr == dst->ptr) goto bad;
+            const double *sp = (const double *)src->ptr, *kp = (const double *)kap->ptr;
+            double *dp = (double *)dst->ptr;
+            hxc_varcoef2d_args v = a;
+            op = [=](cudaStream_t s) {
+                return k::vc_step_otf(sp, dp, kp, v.c, v.ny, v.nx, pc ? &cfg : nullptr, s);
+            };
+            break;
+        }
+        case HXC_K_ADJOINT2D: {
+            ARGS(hxc_adjoint2d_args);
+            if (a.ny <= 0 || a.nx <= 0 || !cfg_ok(pc, 32, 1024)) goto bad;
+            size_t bytes = (size_t)a.ny * a.nx * 8;
+            BUF(li, a.lam_in, bytes, "adjoint2d.lam_in");
+            BUF(lo, a.lam_out, bytes, "adjoint2d.lam_out");
+            BUF(ub, a.u, bytes, "adjoint2d.u");
+            BUF(kap, a.kappa, bytes, "adjoint2d.kappa");
+            BUF(gk, a.grad_kappa, bytes, "adjoint2d.grad_kappa");
+            if (li->ptr == lo->ptr || lo->ptr == ub->ptr || lo->ptr == gk->ptr ||
+                li->ptr == gk->ptr || ub->ptr == gk->ptr || kap->ptr == gk->ptr ||
+                kap->ptr == lo->ptr)
+                goto bad;
+            const double *lip = (const double *)li->ptr, *up = (const double *)ub->ptr,
+                         *kp = (const double *)kap->ptr;
+            double *lop = (double *)lo->ptr, *gp = (double *)gk->ptr;
+            hxc_adjoint2d_args v = a;
+            op = [=](cudaStream_t s) {
+                return k::vc_adjoint_otf(lip, lop, up, kp, gp, v.c, v.ny, v.nx, pc ? &cfg : nullptr,
+                                         s);
+            };
+            break;
+        }
         default:
             set_error("hxc_launch: unknown or unavailable kernel id %d", (int)id);
             return HXC_E_UNSUPPORTED;

@@ -12,93 +12,21 @@
 #include <map>
 #include <memory>
 
+#include "drivers_util.hpp"
 #include "kernels.cuh"
 #include "runtime.hpp"
 
 using namespace hxc;
+using namespace hxc::drv;
 
-namespace {
-
-constexpr int kCopySlot0 = 224;  // slots used for snapshot device->host copies
-constexpr int kCopySlots = 16;
-
-// Partition bounds: [bounds[p], bounds[p+1]).  With `even` the interior
-// bounds are even (keeps 16-byte alignment of rows of doubles).
-std::vector<int64_t> split(int64_t n, int64_t parts, bool even) {
-    std::vector<int64_t> b(parts + 1);
-    for (int64_t p = 0; p <= parts; p++) {
-        if (p == parts)
-            b[p] = n;
-        else if (even && n % 2 == 0)
-            b[p] = (p * (n / 2) / parts) * 2;
-        else
-            b[p] = p * n / parts;
-    }
-    return b;
-}
-
-struct Stats {
-    hxc_run_stats *s;
-    void launch(int64_t k = 1) {
-        if (s) s->kernel_launches += k;
-    }
-    void copy(int64_t h2d, int64_t d2h) {
-        if (!s) return;
-        s->copies++;
-        s->h2d_bytes += h2d;
-        s->d2h_bytes += d2h;
-    }
-};
-
-// Cache of captured graphs, keyed by the full description of the captured
-// work (buffers, shapes, parameters).
+namespace hxc {
+namespace drv {
 std::mutex g_graph_m;
 std::map<std::string, Ref<Graph>> g_graphs;
+}  // namespace drv
+}  // namespace hxc
 
-std::string key_of(const char *what, std::initializer_list<double> vals,
-                   std::initializer_list<const void *> ptrs) {
-    std::string k = what;
-    char buf[64];
-    for (double v : vals) {
-        snprintf(buf, sizeof buf, "|%.17g", v);
-        k += buf;
-    }
-    for (const void *p : ptrs) {
-        snprintf(buf, sizeof buf, "|%p", p);
-        k += buf;
-    }
-    return k;
-}
-
-hxc_status finish(Device *dev, std::vector<FutRef> &finals, hxc_future *out) {
-    FutRef r;
-    // join on the host only if some final future is host work
-    bool host = false;
-    for (auto &f : finals) {
-        std::lock_guard<std::mutex> g(f->m);
-        host |= f->state == Future::PENDING || (f->state == Future::DONE && !f->dev);
-    }
-    if (!host) {
-        hxc_status st = issue_device_op(dev, kJoinSlot, finals, StreamOp(), {}, &r);
-        if (st) return st;
-    } else {
-        r = make_pending();
-        struct J {
-            std::atomic<int> left{0};
-            std::atomic<int> failed{0};
-        };
-        auto j = std::make_shared<J>();
-        j->left = (int)finals.size();
-        if (finals.empty()) fut_set_done(r, HXC_OK);
-        for (auto &f : finals)
-            fut_on_done(f, [r, j](hxc_status s) {
-                if (s != HXC_OK) j->failed = 1;
-                if (j->left.fetch_sub(1) == 1) fut_set_done(r, j->failed ? HXC_E_DEP_FAILED : HXC_OK);
-            });
-    }
-    if (out) *out = to_handle(r);
-    return HXC_OK;
-}
+namespace {
 
 // ---------------------------------------------------------------- 1D runs
 struct Heat1dPlan {
@@ -174,54 +102,6 @@ hxc_status issue_heat1d(const Heat1dPlan &pl, int steps, int T, int &flip, std::
         flip = 1 - flip;
     }
     return HXC_OK;
-}
-
-// True if some dependency is host work that has not finished.
-bool has_pending_host(const std::vector<FutRef> &dv) {
-    for (auto &f : dv) {
-        std::lock_guard<std::mutex> g(f->m);
-        if (f->state == Future::PENDING) return true;
-    }
-    return false;
-}
-
-// Issues a whole run later: once every dependency is done, `issue` runs on
-// the worker pool; the returned futures follow the ones it produces.
-using RunIssue = std::function<hxc_status(FutRef *all, FutRef *field)>;
-
-void defer_run(const std::vector<FutRef> &dv, RunIssue issue, FutRef *all_out, FutRef *field_out) {
-    FutRef a = make_pending(), b = make_pending();
-    struct J {
-        std::atomic<int> left{0};
-        std::atomic<int> failed{0};
-    };
-    auto js = std::make_shared<J>();
-    js->left = (int)dv.size();
-    auto fire = [a, b, js, issue]() {
-        if (js->failed) {
-            fut_set_done(a, HXC_E_DEP_FAILED);
-            fut_set_done(b, HXC_E_DEP_FAILED);
-            return;
-        }
-        pool().submit([a, b, issue] {
-            FutRef ia, ib;
-            hxc_status st = issue(&ia, &ib);
-            if (st) {
-                fut_set_done(a, st);
-                fut_set_done(b, st);
-                return;
-            }
-            fut_on_done(ia, [a](hxc_status s) { fut_set_done(a, s); });
-            fut_on_done(ib ? ib : ia, [b](hxc_status s) { fut_set_done(b, s); });
-        });
-    };
-    for (auto &f : dv)
-        fut_on_done(f, [js, fire](hxc_status s) {
-            if (s != HXC_OK) js->failed = 1;
-            if (js->left.fetch_sub(1) == 1) fire();
-        });
-    *all_out = a;
-    *field_out = b;
 }
 
 }  // namespace

@@ -1,0 +1,398 @@
+// Variable-diffusivity 2D FTCS (conservative flux form) and its adjoint.
+//
+// Method: u'_a = u_a + c * sum_{f in W,E,N,S} k_f (u_b - u_a) with face
+// conductance k_f = (kappa_a + kappa_b) / 2, Dirichlet-zero ghosts whose
+// diffusivity equals the facing interior cell (k_f = kappa_a on a boundary
+// face).  Algebraically u' = m_a u_a + sum_f w_f u_b with w_f = c k_f and
+// m_a = 1 - sum_f w_f (boundary faces included in m, their u_b = 0), which
+// is how the kernels evaluate it: the coefficients are computed once per
+// problem and every step costs 5 FP64 operations.
+//
+// Canonical coefficients (bit-identical wherever computed):
+//   h = 0.5 * kappa;  k_E = h_a + h_{a+1} (interior) or kappa_a (boundary)
+//   w_f = c * k_f;    m = 1 - ((w_W + w_E) + (w_N + w_S))
+//   stored: wE[a] = w_E (0 on the east boundary), wS[a] = w_S (0 on the south
+//   boundary), m[a]; the west/north weights of a are wE[a-1] / wS[a-nx].
+// Canonical step (also the adjoint step: the step matrix is symmetric):
+//   u' = fma(wE, uE, fma(wW, uW, fma(wN, uN, fma(wS, uS, m * u))))
+// with zero neighbours (and zero weights) outside the field.
+// Canonical kappa-gradient of one step, given u = u^n and l = lambda^{n+1}:
+//   d_f = u_b - u_a, l_f = l_a - l_b (u_b = l_b = 0 outside), doubled d_f on
+//   boundary faces; S = fma(dW, lW, fma(dE, lE, fma(dN, lN, dS * lS)));
+//   gk_a = fma(c/2, S, gk_a)
+// i.e. dL/dkappa_a = sum_f dk_f/dkappa_a * c (u_b - u_a)(l_a - l_b).
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace hxc {
+namespace k {
+
+struct VcCoef {
+    double wE, wS, m;
+};
+
+__device__ __forceinline__ VcCoef vc_coef_at(const double *__restrict__ kap, double c, int64_t ny,
+                                            int64_t nx, int64_t i, int64_t j) {
+    const int64_t a = i * nx + j;
+    const double ka = __ldg(kap + a);
+    const double ha = __dmul_rn(0.5, ka);
+    const double kW = j > 0 ? __dadd_rn(ha, __dmul_rn(0.5, __ldg(kap + a - 1))) : ka;
+    const double kE = j + 1 < nx ? __dadd_rn(ha, __dmul_rn(0.5, __ldg(kap + a + 1))) : ka;
+    const double kN = i > 0 ? __dadd_rn(ha, __dmul_rn(0.5, __ldg(kap + a - nx))) : ka;
+    const double kS = i + 1 < ny ? __dadd_rn(ha, __dmul_rn(0.5, __ldg(kap + a + nx))) : ka;
+    const double wW = __dmul_rn(c, kW), wE = __dmul_rn(c, kE), wN = __dmul_rn(c, kN),
+                 wS = __dmul_rn(c, kS);
+    VcCoef r;
+    r.m = __dsub_rn(1.0, __dadd_rn(__dadd_rn(wW, wE), __dadd_rn(wN, wS)));
+    r.wE = j + 1 < nx ? wE : 0.0;
+    r.wS = i + 1 < ny ? wS : 0.0;
+    return r;
+}
+
+__device__ __forceinline__ double vc_update(double u, double uW, double uE, double uN, double uS,
+                                            double wW, double wE, double wN, double wS, double m) {
+    return __fma_rn(wE, uE, __fma_rn(wW, uW, __fma_rn(wN, uN, __fma_rn(wS, uS, __dmul_rn(m, u)))));
+}
+
+// One step of one problem at cell (i, j) with stored coefficients.
+__device__ __forceinline__ double vc_step_at(const double *__restrict__ u,
+                                             const double *__restrict__ wE,
+                                             const double *__restrict__ wS,
+                                             const double *__restrict__ m, int64_t ny, int64_t nx,
+                                             int64_t i, int64_t j) {
+    const int64_t a = i * nx + j;
+    const double uW = j > 0 ? u[a - 1] : 0.0, uE = j + 1 < nx ? u[a + 1] : 0.0;
+    const double uN = i > 0 ? u[a - nx] : 0.0, uS = i + 1 < ny ? u[a + nx] : 0.0;
+    const double wW = j > 0 ? wE[a - 1] : 0.0, wN = i > 0 ? wS[a - nx] : 0.0;
+    return vc_update(u[a], uW, uE, uN, uS, wW, wE[a], wN, wS[a], m[a]);
+}
+
+// ------------------------------------------------------------ one problem
+__global__ void k_vc_coef(const double *__restrict__ kap, double c, int64_t ny, int64_t nx,
+                          double *__restrict__ wE, double *__restrict__ wS, double *__restrict__ m) {
+    const int64_t n = ny * nx;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const VcCoef q = vc_coef_at(kap, c, ny, nx, a / nx, a % nx);
+        wE[a] = q.wE;
+        wS[a] = q.wS;
+        m[a] = q.m;
+    }
+}
+
+__global__ void k_vc_step(const double *__restrict__ u, double *__restrict__ un,
+                          const double *__restrict__ wE, const double *__restrict__ wS,
+                          const double *__restrict__ m, int64_t ny, int64_t nx) {
+    // warps walk rows: lanes cover consecutive columns (coalesced)
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t segs = (nx + 31) / 32;
+    for (int64_t w = blockIdx.x * wpb + (threadIdx.x >> 5); w < ny * segs;
+         w += (int64_t)gridDim.x * wpb) {
+        const int64_t i = w / segs, j = (w % segs) * 32 + lane;
+        if (j < nx) un[i * nx + j] = vc_step_at(u, wE, wS, m, ny, nx, i, j);
+    }
+}
+
+// Coefficients computed on the fly (the hxc_launch kernel): same bits.
+__global__ void k_vc_step_otf(const double *__restrict__ u, double *__restrict__ un,
+                              const double *__restrict__ kap, double c, int64_t ny, int64_t nx) {
+    const int64_t n = ny * nx;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a / nx, j = a % nx;
+        const VcCoef q = vc_coef_at(kap, c, ny, nx, i, j);
+        const double wW = j > 0 ? vc_coef_at(kap, c, ny, nx, i, j - 1).wE : 0.0;
+        const double wN = i > 0 ? vc_coef_at(kap, c, ny, nx, i - 1, j).wS : 0.0;
+        const double uW = j > 0 ? u[a - 1] : 0.0, uE = j + 1 < nx ? u[a + 1] : 0.0;
+        const double uN = i > 0 ? u[a - nx] : 0.0, uS = i + 1 < ny ? u[a + nx] : 0.0;
+        un[a] = vc_update(u[a], uW, uE, uN, uS, wW, q.wE, wN, q.wS, q.m);
+    }
+}
+
+// kappa-gradient contribution of one step at cell (i, j).
+__device__ __forceinline__ double vc_grad_sum(const double *__restrict__ u,
+                                              const double *__restrict__ lam, int64_t ny,
+                                              int64_t nx, int64_t i, int64_t j) {
+    const int64_t a = i * nx + j;
+    const double ua = u[a], la = lam[a];
+    const double dW = j > 0 ? __dsub_rn(u[a - 1], ua) : __dmul_rn(-2.0, ua);
+    const double lW = j > 0 ? __dsub_rn(la, lam[a - 1]) : la;
+    const double dE = j + 1 < nx ? __dsub_rn(u[a + 1], ua) : __dmul_rn(-2.0, ua);
+    const double lE = j + 1 < nx ? __dsub_rn(la, lam[a + 1]) : la;
+    const double dN = i > 0 ? __dsub_rn(u[a - nx], ua) : __dmul_rn(-2.0, ua);
+    const double lN = i > 0 ? __dsub_rn(la, lam[a - nx]) : la;
+    const double dS = i + 1 < ny ? __dsub_rn(u[a + nx], ua) : __dmul_rn(-2.0, ua);
+    const double lS = i + 1 < ny ? __dsub_rn(la, lam[a + nx]) : la;
+    return __fma_rn(dW, lW, __fma_rn(dE, lE, __fma_rn(dN, lN, __dmul_rn(dS, lS))));
+}
+
+// Adjoint step fused with the kappa-gradient accumulation (either part can
+// be switched off to launch them separately).
+__global__ void k_vc_adjoint(const double *__restrict__ lam, double *__restrict__ lam_out,
+                             const double *__restrict__ u, const double *__restrict__ wE,
+                             const double *__restrict__ wS, const double *__restrict__ m,
+                             double *__restrict__ gk, double ch, int64_t ny, int64_t nx,
+                             int do_lam, int do_grad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t segs = (nx + 31) / 32;
+    for (int64_t w = blockIdx.x * wpb + (threadIdx.x >> 5); w < ny * segs;
+         w += (int64_t)gridDim.x * wpb) {
+        const int64_t i = w / segs, j = (w % segs) * 32 + lane;
+        if (j >= nx) continue;
+        const int64_t a = i * nx + j;
+        if (do_lam) lam_out[a] = vc_step_at(lam, wE, wS, m, ny, nx, i, j);
+        if (do_grad) gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j), gk[a]);
+    }
+}
+
+// Adjoint step with on-the-fly coefficients (the hxc_launch kernel).
+__global__ void k_vc_adjoint_otf(const double *__restrict__ lam, double *__restrict__ lam_out,
+                                 const double *__restrict__ u, const double *__restrict__ kap,
+                                 double *__restrict__ gk, double c, int64_t ny, int64_t nx) {
+    const int64_t n = ny * nx;
+    const double ch = __dmul_rn(0.5, c);
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a / nx, j = a % nx;
+        const VcCoef q = vc_coef_at(kap, c, ny, nx, i, j);
+        const double wW = j > 0 ? vc_coef_at(kap, c, ny, nx, i, j - 1).wE : 0.0;
+        const double wN = i > 0 ? vc_coef_at(kap, c, ny, nx, i - 1, j).wS : 0.0;
+        const double lW = j > 0 ? lam[a - 1] : 0.0, lE = j + 1 < nx ? lam[a + 1] : 0.0;
+        const double lN = i > 0 ? lam[a - nx] : 0.0, lS = i + 1 < ny ? lam[a + nx] : 0.0;
+        lam_out[a] = vc_update(lam[a], lW, lE, lN, lS, wW, q.wE, wN, q.wS, q.m);
+        gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j), gk[a]);
+    }
+}
+
+// Squared error and adjoint seed: lam = 2 (u - t); partial sums of (u - t)^2
+// in a fixed order (grid of kSqBlocks CTAs, element k to thread k mod
+// (kSqBlocks*256) accumulated in increasing k, then a fixed tree), the last
+// CTA adds the partials in order and stores the loss.
+constexpr int kSqBlocks = 256;
+__global__ void __launch_bounds__(256) k_sqerr_seed(const double *__restrict__ u,
+                                                    const double *__restrict__ t,
+                                                    double *__restrict__ lam, int64_t n,
+                                                    double *partials, unsigned *counter,
+                                                    double *loss) {
+    const int64_t stride = (int64_t)kSqBlocks * 256;
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * 256 + threadIdx.x; k < n; k += stride) {
+        const double d = __dsub_rn(u[k], t[k]);
+        if (lam) lam[k] = __dmul_rn(2.0, d);
+        acc = __fma_rn(d, d, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    __shared__ double ws[8];
+    __shared__ bool is_last;
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double s = __dadd_rn(__dadd_rn(__dadd_rn(ws[0], ws[1]), __dadd_rn(ws[2], ws[3])),
+                                   __dadd_rn(__dadd_rn(ws[4], ws[5]), __dadd_rn(ws[6], ws[7])));
+        partials[blockIdx.x] = s;
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == kSqBlocks - 1;
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (int q = 0; q < kSqBlocks; q++) s = __dadd_rn(s, __ldcg(partials + q));
+        *loss = s;
+        *counter = 0u;  // leave the scratch ready for the next launch
+    }
+}
+
+// --------------------------------------------------------------- batches
+// Problem descriptor of a batch (problems packed back to back).
+struct VcProblem {
+    int64_t off;
+    int32_t side;
+    int32_t pad;
+    double c;
+};
+
+// Persistent batch kernel: every CTA takes whole problems from a work queue
+// (largest first) and runs all `steps` steps of a problem before taking the
+// next one, so the batch is a single launch with no device-wide barrier.
+// The CTA computes the problem's coefficients into wE/wS/m first; steps
+// ping-pong between u and tmp; an odd step count ends with a copy into u.
+__global__ void __launch_bounds__(256) k_vc_batch(const VcProblem *__restrict__ probs, int nprob,
+                                                  unsigned *queue, double *u, double *tmp,
+                                                  const double *__restrict__ kap, double *wE,
+                                                  double *wS, double *m, int steps) {
+    __shared__ int item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) item = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int p = item;
+        __syncthreads();
+        if (p >= nprob) break;
+        const VcProblem pr = probs[p];
+        const int64_t s = pr.side, n = s * s, off = pr.off;
+        double *pu = u + off, *pt = tmp + off, *pe = wE + off, *ps = wS + off, *pm = m + off;
+        const double *pk = kap + off;
+        for (int64_t a = threadIdx.x; a < n; a += blockDim.x) {
+            const VcCoef q = vc_coef_at(pk, pr.c, s, s, a / s, a % s);
+            pe[a] = q.wE;
+            ps[a] = q.wS;
+            pm[a] = q.m;
+        }
+        __syncthreads();
+        for (int st = 0; st < steps; st++) {
+            const double *src = (st & 1) ? pt : pu;
+            double *dst = (st & 1) ? pu : pt;
+            for (int64_t i = warp; i < s; i += nw)
+                for (int64_t j = lane; j < s; j += 32)
+                    dst[i * s + j] = vc_step_at(src, pe, ps, pm, s, s, i, j);
+            __syncthreads();
+        }
+        if (steps & 1) {
+            for (int64_t a = threadIdx.x; a < n; a += blockDim.x) pu[a] = pt[a];
+            __syncthreads();
+        }
+    }
+}
+
+// Batched coefficient and step kernels for the per-step schedule: the work
+// is the list of rows of all problems; row r belongs to the problem whose
+// row range [rows[p], rows[p+1]) contains it.
+__device__ __forceinline__ int find_problem(const int64_t *__restrict__ rows, int nprob, int64_t r) {
+    int lo = 0, hi = nprob;  // rows[lo] <= r < rows[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(rows + mid) <= r)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_vc_batch_coef(const VcProblem *__restrict__ probs, const int64_t *__restrict__ rows,
+                                int nprob, const double *__restrict__ kap, double *wE, double *wS,
+                                double *m) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5, total = rows[nprob];
+    for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < total; r += (int64_t)gridDim.x * wpb) {
+        const int p = find_problem(rows, nprob, r);
+        const VcProblem pr = probs[p];
+        const int64_t s = pr.side, i = r - rows[p];
+        for (int64_t j = lane; j < s; j += 32) {
+            const VcCoef q = vc_coef_at(kap + pr.off, pr.c, s, s, i, j);
+            const int64_t a = pr.off + i * s + j;
+            wE[a] = q.wE;
+            wS[a] = q.wS;
+            m[a] = q.m;
+        }
+    }
+}
+
+__global__ void k_vc_batch_step(const VcProblem *__restrict__ probs, const int64_t *__restrict__ rows,
+                                int nprob, const double *__restrict__ u, double *__restrict__ un,
+                                const double *__restrict__ wE, const double *__restrict__ wS,
+                                const double *__restrict__ m) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5, total = rows[nprob];
+    for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < total; r += (int64_t)gridDim.x * wpb) {
+        const int p = find_problem(rows, nprob, r);
+        const VcProblem pr = probs[p];
+        const int64_t s = pr.side, i = r - rows[p], o = pr.off;
+        for (int64_t j = lane; j < s; j += 32)
+            un[o + i * s + j] = vc_step_at(u + o, wE + o, wS + o, m + o, s, s, i, j);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static unsigned grid_for(int64_t work, unsigned per_block, const hxc_launch_cfg *cfg) {
+    if (cfg) return cfg->grid[0] * cfg->grid[1] * cfg->grid[2];
+    int64_t g = (work + per_block - 1) / per_block;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sm_count() * 16));
+}
+
+cudaError_t vc_coef(const double *kap, double c, int64_t ny, int64_t nx, double *wE, double *wS,
+                    double *m, cudaStream_t s) {
+    k_vc_coef<<<grid_for(ny * nx, 256, nullptr), 256, 0, s>>>(kap, c, ny, nx, wE, wS, m);
+    return cudaGetLastError();
+}
+
+cudaError_t vc_step(const double *u, double *un, const double *wE, const double *wS,
+                    const double *m, int64_t ny, int64_t nx, cudaStream_t s) {
+    const int64_t work = ny * ((nx + 31) / 32);
+    k_vc_step<<<grid_for(work, 8, nullptr), 256, 0, s>>>(u, un, wE, wS, m, ny, nx);
+    return cudaGetLastError();
+}
+
+cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c, int64_t ny,
+                        int64_t nx, const hxc_launch_cfg *cfg, cudaStream_t s) {
+    unsigned b = cfg ? cfg->block[0] * cfg->block[1] * cfg->block[2] : 256;
+    k_vc_step_otf<<<grid_for(ny * nx, b, cfg), b, 0, s>>>(u, un, kap, c, ny, nx);
+    return cudaGetLastError();
+}
+
+cudaError_t vc_adjoint(const double *lam, double *lam_out, const double *u, const double *wE,
+                       const double *wS, const double *m, double *gk, double c, int64_t ny,
+                       int64_t nx, bool do_lam, bool do_grad, cudaStream_t s) {
+    const int64_t work = ny * ((nx + 31) / 32);
+    k_vc_adjoint<<<grid_for(work, 8, nullptr), 256, 0, s>>>(lam, lam_out, u, wE, wS, m, gk,
+                                                          0.5 * c, ny, nx, do_lam, do_grad);
+    return cudaGetLastError();
+}
+
+cudaError_t vc_adjoint_otf(const double *lam, double *lam_out, const double *u, const double *kap,
+                           double *gk, double c, int64_t ny, int64_t nx, const hxc_launch_cfg *cfg,
+                           cudaStream_t s) {
+    unsigned b = cfg ? cfg->block[0] * cfg->block[1] * cfg->block[2] : 256;
+    k_vc_adjoint_otf<<<grid_for(ny * nx, b, cfg), b, 0, s>>>(lam, lam_out, u, kap, gk, c, ny, nx);
+    return cudaGetLastError();
+}
+
+cudaError_t sqerr_seed(const double *u, const double *t, double *lam, int64_t n, void *scratch,
+                       double *loss, cudaStream_t s) {
+    double *partials = static_cast<double *>(scratch);
+    unsigned *counter = reinterpret_cast<unsigned *>(partials + kSqBlocks);
+    k_sqerr_seed<<<kSqBlocks, 256, 0, s>>>(u, t, lam, n, partials, counter, loss);
+    return cudaGetLastError();
+}
+
+size_t sqerr_scratch_bytes() { return kSqBlocks * sizeof(double) + 16; }
+
+cudaError_t vc_batch_persistent(const void *probs, int nprob, unsigned *queue, double *u,
+                                double *tmp, const double *kap, double *wE, double *wS, double *m,
+                                int steps, int ctas_per_sm, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int g = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 4);
+    k_vc_batch<<<g, 256, 0, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
+                                  wE, wS, m, steps);
+    return cudaGetLastError();
+}
+
+cudaError_t vc_batch_coef(const void *probs, const int64_t *rows, int nprob, int64_t total_rows,
+                          const double *kap, double *wE, double *wS, double *m, cudaStream_t s) {
+    k_vc_batch_coef<<<grid_for(total_rows, 8, nullptr), 256, 0, s>>>(
+        static_cast<const VcProblem *>(probs), rows, nprob, kap, wE, wS, m);
+    return cudaGetLastError();
+}
+
+cudaError_t vc_batch_step(const void *probs, const int64_t *rows, int nprob, int64_t total_rows,
+                          const double *u, double *un, const double *wE, const double *wS,
+                          const double *m, cudaStream_t s) {
+    k_vc_batch_step<<<grid_for(total_rows, 8, nullptr), 256, 0, s>>>(
+        static_cast<const VcProblem *>(probs), rows, nprob, u, un, wE, wS, m);
+    return cudaGetLastError();
+}
+
+size_t vc_problem_bytes() { return sizeof(VcProblem); }
+
+void vc_pack_problem(void *dst, int64_t off, int32_t side, double c) {
+    VcProblem p{off, side, 0, c};
+    *static_cast<VcProblem *>(dst) = p;
+}
+
+}  // namespace k
+}  // namespace hxc

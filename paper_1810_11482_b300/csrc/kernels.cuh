@@ -53,5 +53,33 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
                    int zchunk, const hxc_launch_cfg *cfg, cudaStream_t s);
 int heat3d_default_zchunk(int nz, int ny, int nx, int T);
 
+// Variable-diffusivity step (coefficients precomputed by vc_coef or on the
+// fly), adjoint step with kappa-gradient, squared-error seed, batches.
+cudaError_t vc_coef(const double *kap, double c, int64_t ny, int64_t nx, double *wE, double *wS,
+                    double *m, cudaStream_t s);
+cudaError_t vc_step(const double *u, double *un, const double *wE, const double *wS,
+                    const double *m, int64_t ny, int64_t nx, cudaStream_t s);
+cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c, int64_t ny,
+                        int64_t nx, const hxc_launch_cfg *cfg, cudaStream_t s);
+cudaError_t vc_adjoint(const double *lam, double *lam_out, const double *u, const double *wE,
+                       const double *wS, const double *m, double *gk, double c, int64_t ny,
+                       int64_t nx, bool do_lam, bool do_grad, cudaStream_t s);
+cudaError_t vc_adjoint_otf(const double *lam, double *lam_out, const double *u, const double *kap,
+                           double *gk, double c, int64_t ny, int64_t nx, const hxc_launch_cfg *cfg,
+                           cudaStream_t s);
+cudaError_t sqerr_seed(const double *u, const double *t, double *lam, int64_t n, void *scratch,
+                       double *loss, cudaStream_t s);
+size_t sqerr_scratch_bytes();
+cudaError_t vc_batch_persistent(const void *probs, int nprob, unsigned *queue, double *u,
+                                double *tmp, const double *kap, double *wE, double *wS, double *m,
+                                int steps, int ctas_per_sm, cudaStream_t s);
+cudaError_t vc_batch_coef(const void *probs, const int64_t *rows, int nprob, int64_t total_rows,
+                          const double *kap, double *wE, double *wS, double *m, cudaStream_t s);
+cudaError_t vc_batch_step(const void *probs, const int64_t *rows, int nprob, int64_t total_rows,
+                          const double *u, double *un, const double *wE, const double *wS,
+                          const double *m, cudaStream_t s);
+size_t vc_problem_bytes();
+void vc_pack_problem(void *dst, int64_t off, int32_t side, double c);
+
 }  // namespace k
 }  // namespace hxc

@@ -195,6 +195,7 @@ struct Graph : RefCounted {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t nodes = 0;
+    int64_t kernels = 0;  // kernels one replay launches (set by the capturer)
     std::vector<AnyRef> keep;
     ~Graph() override;
 };

@@ -51,7 +51,7 @@ c_st = ctypes.c_int
 i64 = ctypes.c_int64
 HOST_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
 # argument structs beyond the core set, checked against the header by the tests
-EXTRA_STRUCTS = ["hxc_heat3d_args"]
+EXTRA_STRUCTS = ["hxc_heat3d_args", "hxc_varcoef2d_args", "hxc_adjoint2d_args"]
 
 
 class hxc_launch_cfg(ctypes.Structure):
@@ -84,6 +84,16 @@ class hxc_tile_norm2_args(ctypes.Structure):
 class hxc_heat3d_args(ctypes.Structure):
     _fields_ = [("src", c_buf), ("dst", c_buf), ("nz", i64), ("ny", i64), ("nx", i64),
                 ("r", ctypes.c_float), ("steps", ctypes.c_int32)]
+
+
+class hxc_varcoef2d_args(ctypes.Structure):
+    _fields_ = [("src", c_buf), ("dst", c_buf), ("kappa", c_buf), ("ny", i64), ("nx", i64),
+                ("c", ctypes.c_double)]
+
+
+class hxc_adjoint2d_args(ctypes.Structure):
+    _fields_ = [("lam_in", c_buf), ("lam_out", c_buf), ("u", c_buf), ("kappa", c_buf),
+                ("grad_kappa", c_buf), ("ny", i64), ("nx", i64), ("c", ctypes.c_double)]
 
 
 class hxc_partition_args(ctypes.Structure):
@@ -177,6 +187,19 @@ _SIGS = {
     "hxc_heat3d_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, i64, ctypes.c_float, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.POINTER(c_fut), ctypes.c_int,
                               ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_varcoef_batch_run": (c_st, [c_dev, c_buf, c_buf, ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_double), i64, ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(c_fut), ctypes.c_int,
+                                     ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_sqerr_seed": (c_st, [c_dev, c_buf, c_buf, c_buf, c_buf, i64, ctypes.c_int,
+                              ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut)]),
+    "hxc_varcoef_adjoint_run": (c_st, [c_dev, c_buf, c_buf, c_buf, i64, i64, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, c_buf, c_buf,
+                                       c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
+                                       ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
+                                       ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
+                                       ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
     "hxc_heat2d_run_host": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.POINTER(hxc_heat2d_cfg), ctypes.POINTER(hxc_run_stats)]),
 }
@@ -407,6 +430,48 @@ def heat3d_run(dev, u, tmp, shape, r, steps, mode="fused", steps_per_launch=0, d
     check(lib().hxc_heat3d_run(dev.h, u.h, tmp.h, nz, ny, nx, r, steps, MODES[mode],
                                steps_per_launch, arr, nd, ctypes.byref(out), ctypes.byref(st)),
           "heat3d_run")
+    return Future(out.value), st
+
+
+def varcoef_batch_run(dev, u, kappa, sides, cs, steps, mode="fused", deps=()):
+    sides = np.ascontiguousarray(sides, dtype=np.int64)
+    cs = np.ascontiguousarray(cs, dtype=np.float64)
+    arr, nd = _futs(deps)
+    out = c_fut()
+    st = hxc_run_stats()
+    check(lib().hxc_varcoef_batch_run(dev.h, u.h, kappa.h, sides.ctypes.data_as(ctypes.POINTER(i64)),
+                                      cs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      sides.size, steps, MODES[mode], arr, nd, ctypes.byref(out),
+                                      ctypes.byref(st)), "varcoef_batch_run")
+    return Future(out.value), st
+
+
+def sqerr_seed(dev, u, t, lam, loss, n, slot=0, deps=()):
+    arr, nd = _futs(deps)
+    out = c_fut()
+    check(lib().hxc_sqerr_seed(dev.h, u.h, t.h, lam.h if lam is not None else None, loss.h, n,
+                               slot, arr, nd, ctypes.byref(out)), "sqerr_seed")
+    return Future(out.value)
+
+
+def varcoef_forward_run(dev, u0, kappa, ny, nx, c, steps, uT, deps=()):
+    arr, nd = _futs(deps)
+    out = c_fut()
+    st = hxc_run_stats()
+    check(lib().hxc_varcoef_forward_run(dev.h, u0.h, kappa.h, ny, nx, c, steps, uT.h, arr, nd,
+                                        ctypes.byref(out), ctypes.byref(st)), "varcoef_forward_run")
+    return Future(out.value), st
+
+
+def varcoef_adjoint_run(dev, u0, kappa, lamT, ny, nx, c, steps, gk, gu0, uT=None, every=0,
+                        mode="fused", deps=()):
+    arr, nd = _futs(deps)
+    out = c_fut()
+    st = hxc_run_stats()
+    check(lib().hxc_varcoef_adjoint_run(dev.h, u0.h, kappa.h, lamT.h, ny, nx, c, steps, every,
+                                        MODES[mode], gk.h, gu0.h, uT.h if uT is not None else None,
+                                        arr, nd, ctypes.byref(out), ctypes.byref(st)),
+          "varcoef_adjoint_run")
     return Future(out.value), st
 
 
