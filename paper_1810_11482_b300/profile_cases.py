@@ -1,0 +1,69 @@
+"""Small, self-contained cases for profiling one kernel at a time.
+
+    python -m paper_1810_11482_b300.profile_cases heat2d [n] [launches]
+    python -m paper_1810_11482_b300.profile_cases heat3d [nz ny nx] [steps]
+    python -m paper_1810_11482_b300.profile_cases batch [nprob] [steps]
+    python -m paper_1810_11482_b300.profile_cases adjoint [n] [steps]
+
+Each case uploads seeded synthetic inputs, runs the path once through the C
+ABI and exits 0; sizes default to fields larger than the 126 MB L2 but small
+enough for a profiler capture.
+"""
+import sys
+
+import numpy as np
+
+from . import hxc, synth
+
+
+def heat2d(n=4096, launches=3):
+    dev = hxc.get_all_devices(2, 0)[0]
+    u0 = synth.uniform(5, n * n).reshape(n, n)
+    u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    u.write(u0).get()
+    cfg = hxc.heat2d_cfg(n, n, 1, 1, 0.2, launches, 0, "fused", None, None)
+    f, st = hxc.heat2d_run(dev, u, t, cfg)
+    f.get()
+    return st.kernel_launches
+
+
+def heat3d(nz=256, ny=512, nx=512, steps=8):
+    dev = hxc.get_all_devices(2, 0)[0]
+    u0 = synth.uniform(6, nz * ny * nx).astype(np.float32)
+    u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    u.write(u0).get()
+    f, st = hxc.heat3d_run(dev, u, t, (nz, ny, nx), 0.15, steps, "fused", 4)
+    f.get()
+    return st.kernel_launches
+
+
+def batch(nprob=512, steps=10):
+    dev = hxc.get_all_devices(2, 0)[0]
+    sides, offs, kap, u0, cs = synth.batch_input(nprob=nprob, seed=4)
+    u, k = dev.buffer(u0.nbytes), dev.buffer(kap.nbytes)
+    u.write(u0).get()
+    k.write(kap).get()
+    f, st = hxc.varcoef_batch_run(dev, u, k, sides, cs, steps, "fused")
+    f.get()
+    return st.kernel_launches
+
+
+def adjoint(n=2048, steps=20):
+    dev = hxc.get_all_devices(2, 0)[0]
+    kref, kap, u0, c = synth.adjoint_input(n)
+    bu, bk, bl = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    bu.write(u0).get()
+    bk.write(kap).get()
+    bl.write(u0).get()
+    gk, gu = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    f, st = hxc.varcoef_adjoint_run(dev, bu, bk, bl, n, n, c, steps, gk, gu)
+    f.get()
+    return st.kernel_launches
+
+
+CASES = {"heat2d": heat2d, "heat3d": heat3d, "batch": batch, "adjoint": adjoint}
+
+if __name__ == "__main__":
+    name = sys.argv[1]
+    args = [int(a) for a in sys.argv[2:]]
+    print(name, "launches:", CASES[name](*args))
