@@ -409,6 +409,37 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
                                    const hxc_future *deps, int ndeps, hxc_future *out,
                                    hxc_run_stats *stats);
 
+/* ------------------------------------------- norms without allocation */
+
+/* Largest tile grid (tiles_y * tiles_x) hxc_tile_norms_noalloc accepts. */
+#define HXC_NOALLOC_MAX_TILES 256
+
+/* The paper has no counterpart to this call.  Per-tile L2 norms
+ * sqrt(sum u^2) of a row-major ny x nx field of doubles cut into a
+ * tiles_y x tiles_x grid (rows split at p*ny/tiles_y; columns at
+ * 2*(q*(nx/2)/tiles_x) when nx is even, else q*nx/tiles_x -- the tiles of
+ * hxc_heat2d_run), written to norms[p*tiles_x + q], with the same fixed
+ * reduction order (and so the same bits) as HXC_K_TILE_NORM2.
+ *
+ * It allocates nothing, for callers that must not let the library allocate
+ * device memory: a time-critical loop in which cudaMalloc would synchronise
+ * the device, a process whose device memory belongs to another allocator,
+ * or a deployment that forbids allocation after start-up.  Its reduction
+ * scratch is a fixed array of about 129 KB compiled into the library and
+ * held on every GPU that loads it until the process exits; grids of more
+ * than HXC_NOALLOC_MAX_TILES tiles are rejected with HXC_E_INVALID.
+ *
+ * src and norms are device pointers on the current device, stream a
+ * cudaStream_t (NULL: the legacy default stream); the call is asynchronous
+ * on that stream and returns launch errors only.  The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress) with
+ * that device current: make it before any stream capture.  Every call on a
+ * device shares the one array and clears the counters it needs; calls whose
+ * executions overlap on the GPU (different streams, no ordering) race on
+ * it and must be serialised by the caller. */
+hxc_status hxc_tile_norms_noalloc(const double *src, int64_t ny, int64_t nx, int64_t tiles_y,
+                                  int64_t tiles_x, double *norms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -200,6 +200,8 @@ _SIGS = {
     "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
                                        ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_tile_norms_noalloc": (c_st, [ctypes.c_void_p, i64, i64, i64, i64, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "hxc_heat2d_run_host": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.POINTER(hxc_heat2d_cfg), ctypes.POINTER(hxc_run_stats)]),
 }
