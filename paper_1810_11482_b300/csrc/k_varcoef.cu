@@ -15,6 +15,8 @@
 //   boundary), m[a]; the west/north weights of a are wE[a-1] / wS[a-nx].
 // Canonical step (also the adjoint step: the step matrix is symmetric):
 //   u' = fma(wE, uE, fma(wW, uW, fma(wN, uN, fma(wS, uS, m * u))))
+// (products and differences issued as fused multiply-adds that round
+// identically, see Fk below).
 // with zero neighbours (and zero weights) outside the field.
 // Canonical kappa-gradient of one step, given u = u^n and l = lambda^{n+1}:
 //   d_f = u_b - u_a, l_f = l_a - l_b (u_b = l_b = 0 outside), doubled d_f on
@@ -50,9 +52,19 @@ __device__ __forceinline__ VcCoef vc_coef_at(const double *__restrict__ kap, dou
     return r;
 }
 
+// Run-time constants (kernel arguments, so that the compiler cannot fold
+// them): products and differences are issued as fused multiply-adds, which
+// round identically -- fma(a, b, -0) == a*b, fma(b, -1, a) == a - b -- but
+// issue faster than DMUL/DADD on B300.
+struct Fk {
+    double nz;    // -0.0
+    double mone;  // -1.0
+};
+
 __device__ __forceinline__ double vc_update(double u, double uW, double uE, double uN, double uS,
-                                            double wW, double wE, double wN, double wS, double m) {
-    return __fma_rn(wE, uE, __fma_rn(wW, uW, __fma_rn(wN, uN, __fma_rn(wS, uS, __dmul_rn(m, u)))));
+                                            double wW, double wE, double wN, double wS, double m,
+                                            Fk f) {
+    return __fma_rn(wE, uE, __fma_rn(wW, uW, __fma_rn(wN, uN, __fma_rn(wS, uS, __fma_rn(m, u, f.nz)))));
 }
 
 // One step of one problem at cell (i, j) with stored coefficients.
@@ -60,12 +72,12 @@ __device__ __forceinline__ double vc_step_at(const double *__restrict__ u,
                                              const double *__restrict__ wE,
                                              const double *__restrict__ wS,
                                              const double *__restrict__ m, int64_t ny, int64_t nx,
-                                             int64_t i, int64_t j) {
+                                             int64_t i, int64_t j, Fk f) {
     const int64_t a = i * nx + j;
     const double uW = j > 0 ? u[a - 1] : 0.0, uE = j + 1 < nx ? u[a + 1] : 0.0;
     const double uN = i > 0 ? u[a - nx] : 0.0, uS = i + 1 < ny ? u[a + nx] : 0.0;
     const double wW = j > 0 ? wE[a - 1] : 0.0, wN = i > 0 ? wS[a - nx] : 0.0;
-    return vc_update(u[a], uW, uE, uN, uS, wW, wE[a], wN, wS[a], m[a]);
+    return vc_update(u[a], uW, uE, uN, uS, wW, wE[a], wN, wS[a], m[a], f);
 }
 
 // ------------------------------------------------------------ one problem
@@ -83,7 +95,7 @@ __global__ void k_vc_coef(const double *__restrict__ kap, double c, int64_t ny, 
 
 __global__ void k_vc_step(const double *__restrict__ u, double *__restrict__ un,
                           const double *__restrict__ wE, const double *__restrict__ wS,
-                          const double *__restrict__ m, int64_t ny, int64_t nx) {
+                          const double *__restrict__ m, int64_t ny, int64_t nx, Fk f) {
     // warps walk rows: lanes cover consecutive columns (coalesced)
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
@@ -91,13 +103,14 @@ __global__ void k_vc_step(const double *__restrict__ u, double *__restrict__ un,
     for (int64_t w = blockIdx.x * wpb + (threadIdx.x >> 5); w < ny * segs;
          w += (int64_t)gridDim.x * wpb) {
         const int64_t i = w / segs, j = (w % segs) * 32 + lane;
-        if (j < nx) un[i * nx + j] = vc_step_at(u, wE, wS, m, ny, nx, i, j);
+        if (j < nx) un[i * nx + j] = vc_step_at(u, wE, wS, m, ny, nx, i, j, f);
     }
 }
 
 // Coefficients computed on the fly (the hxc_launch kernel): same bits.
 __global__ void k_vc_step_otf(const double *__restrict__ u, double *__restrict__ un,
-                              const double *__restrict__ kap, double c, int64_t ny, int64_t nx) {
+                              const double *__restrict__ kap, double c, int64_t ny, int64_t nx,
+                              Fk f) {
     const int64_t n = ny * nx;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
          a += (int64_t)gridDim.x * blockDim.x) {
@@ -107,25 +120,26 @@ __global__ void k_vc_step_otf(const double *__restrict__ u, double *__restrict__
         const double wN = i > 0 ? vc_coef_at(kap, c, ny, nx, i - 1, j).wS : 0.0;
         const double uW = j > 0 ? u[a - 1] : 0.0, uE = j + 1 < nx ? u[a + 1] : 0.0;
         const double uN = i > 0 ? u[a - nx] : 0.0, uS = i + 1 < ny ? u[a + nx] : 0.0;
-        un[a] = vc_update(u[a], uW, uE, uN, uS, wW, q.wE, wN, q.wS, q.m);
+        un[a] = vc_update(u[a], uW, uE, uN, uS, wW, q.wE, wN, q.wS, q.m, f);
     }
 }
 
 // kappa-gradient contribution of one step at cell (i, j).
 __device__ __forceinline__ double vc_grad_sum(const double *__restrict__ u,
                                               const double *__restrict__ lam, int64_t ny,
-                                              int64_t nx, int64_t i, int64_t j) {
+                                              int64_t nx, int64_t i, int64_t j, Fk f) {
     const int64_t a = i * nx + j;
     const double ua = u[a], la = lam[a];
-    const double dW = j > 0 ? __dsub_rn(u[a - 1], ua) : __dmul_rn(-2.0, ua);
-    const double lW = j > 0 ? __dsub_rn(la, lam[a - 1]) : la;
-    const double dE = j + 1 < nx ? __dsub_rn(u[a + 1], ua) : __dmul_rn(-2.0, ua);
-    const double lE = j + 1 < nx ? __dsub_rn(la, lam[a + 1]) : la;
-    const double dN = i > 0 ? __dsub_rn(u[a - nx], ua) : __dmul_rn(-2.0, ua);
-    const double lN = i > 0 ? __dsub_rn(la, lam[a - nx]) : la;
-    const double dS = i + 1 < ny ? __dsub_rn(u[a + nx], ua) : __dmul_rn(-2.0, ua);
-    const double lS = i + 1 < ny ? __dsub_rn(la, lam[a + nx]) : la;
-    return __fma_rn(dW, lW, __fma_rn(dE, lE, __fma_rn(dN, lN, __dmul_rn(dS, lS))));
+    const double db = __fma_rn(-2.0, ua, f.nz);  // boundary face: 2 (0 - u_a)
+    const double dW = j > 0 ? __fma_rn(ua, f.mone, u[a - 1]) : db;
+    const double lW = j > 0 ? __fma_rn(lam[a - 1], f.mone, la) : la;
+    const double dE = j + 1 < nx ? __fma_rn(ua, f.mone, u[a + 1]) : db;
+    const double lE = j + 1 < nx ? __fma_rn(lam[a + 1], f.mone, la) : la;
+    const double dN = i > 0 ? __fma_rn(ua, f.mone, u[a - nx]) : db;
+    const double lN = i > 0 ? __fma_rn(lam[a - nx], f.mone, la) : la;
+    const double dS = i + 1 < ny ? __fma_rn(ua, f.mone, u[a + nx]) : db;
+    const double lS = i + 1 < ny ? __fma_rn(lam[a + nx], f.mone, la) : la;
+    return __fma_rn(dW, lW, __fma_rn(dE, lE, __fma_rn(dN, lN, __fma_rn(dS, lS, f.nz))));
 }
 
 // Adjoint step fused with the kappa-gradient accumulation (either part can
@@ -134,7 +148,7 @@ __global__ void k_vc_adjoint(const double *__restrict__ lam, double *__restrict_
                              const double *__restrict__ u, const double *__restrict__ wE,
                              const double *__restrict__ wS, const double *__restrict__ m,
                              double *__restrict__ gk, double ch, int64_t ny, int64_t nx,
-                             int do_lam, int do_grad) {
+                             int do_lam, int do_grad, Fk f) {
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t segs = (nx + 31) / 32;
@@ -143,15 +157,16 @@ __global__ void k_vc_adjoint(const double *__restrict__ lam, double *__restrict_
         const int64_t i = w / segs, j = (w % segs) * 32 + lane;
         if (j >= nx) continue;
         const int64_t a = i * nx + j;
-        if (do_lam) lam_out[a] = vc_step_at(lam, wE, wS, m, ny, nx, i, j);
-        if (do_grad) gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j), gk[a]);
+        if (do_lam) lam_out[a] = vc_step_at(lam, wE, wS, m, ny, nx, i, j, f);
+        if (do_grad) gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j, f), gk[a]);
     }
 }
 
 // Adjoint step with on-the-fly coefficients (the hxc_launch kernel).
 __global__ void k_vc_adjoint_otf(const double *__restrict__ lam, double *__restrict__ lam_out,
                                  const double *__restrict__ u, const double *__restrict__ kap,
-                                 double *__restrict__ gk, double c, int64_t ny, int64_t nx) {
+                                 double *__restrict__ gk, double c, int64_t ny, int64_t nx,
+                                 Fk f) {
     const int64_t n = ny * nx;
     const double ch = __dmul_rn(0.5, c);
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
@@ -162,8 +177,8 @@ __global__ void k_vc_adjoint_otf(const double *__restrict__ lam, double *__restr
         const double wN = i > 0 ? vc_coef_at(kap, c, ny, nx, i - 1, j).wS : 0.0;
         const double lW = j > 0 ? lam[a - 1] : 0.0, lE = j + 1 < nx ? lam[a + 1] : 0.0;
         const double lN = i > 0 ? lam[a - nx] : 0.0, lS = i + 1 < ny ? lam[a + nx] : 0.0;
-        lam_out[a] = vc_update(lam[a], lW, lE, lN, lS, wW, q.wE, wN, q.wS, q.m);
-        gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j), gk[a]);
+        lam_out[a] = vc_update(lam[a], lW, lE, lN, lS, wW, q.wE, wN, q.wS, q.m, f);
+        gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j, f), gk[a]);
     }
 }
 
@@ -223,7 +238,7 @@ struct VcProblem {
 __global__ void __launch_bounds__(256) k_vc_batch(const VcProblem *__restrict__ probs, int nprob,
                                                   unsigned *queue, double *u, double *tmp,
                                                   const double *__restrict__ kap, double *wE,
-                                                  double *wS, double *m, int steps) {
+                                                  double *wS, double *m, int steps, Fk f) {
     __shared__ int item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (;;) {
@@ -248,7 +263,7 @@ __global__ void __launch_bounds__(256) k_vc_batch(const VcProblem *__restrict__ 
             double *dst = (st & 1) ? pu : pt;
             for (int64_t i = warp; i < s; i += nw)
                 for (int64_t j = lane; j < s; j += 32)
-                    dst[i * s + j] = vc_step_at(src, pe, ps, pm, s, s, i, j);
+                    dst[i * s + j] = vc_step_at(src, pe, ps, pm, s, s, i, j, f);
             __syncthreads();
         }
         if (steps & 1) {
@@ -295,7 +310,7 @@ __global__ void k_vc_batch_coef(const VcProblem *__restrict__ probs, const int64
 __global__ void k_vc_batch_step(const VcProblem *__restrict__ probs, const int64_t *__restrict__ rows,
                                 int nprob, const double *__restrict__ u, double *__restrict__ un,
                                 const double *__restrict__ wE, const double *__restrict__ wS,
-                                const double *__restrict__ m) {
+                                const double *__restrict__ m, Fk f) {
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5, total = rows[nprob];
     for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < total; r += (int64_t)gridDim.x * wpb) {
@@ -303,11 +318,13 @@ __global__ void k_vc_batch_step(const VcProblem *__restrict__ probs, const int64
         const VcProblem pr = probs[p];
         const int64_t s = pr.side, i = r - rows[p], o = pr.off;
         for (int64_t j = lane; j < s; j += 32)
-            un[o + i * s + j] = vc_step_at(u + o, wE + o, wS + o, m + o, s, s, i, j);
+            un[o + i * s + j] = vc_step_at(u + o, wE + o, wS + o, m + o, s, s, i, j, f);
     }
 }
 
 // ---------------------------------------------------------------- launchers
+static const Fk kF{-0.0, -1.0};
+
 static unsigned grid_for(int64_t work, unsigned per_block, const hxc_launch_cfg *cfg) {
     if (cfg) return cfg->grid[0] * cfg->grid[1] * cfg->grid[2];
     int64_t g = (work + per_block - 1) / per_block;
@@ -323,14 +340,14 @@ cudaError_t vc_coef(const double *kap, double c, int64_t ny, int64_t nx, double 
 cudaError_t vc_step(const double *u, double *un, const double *wE, const double *wS,
                     const double *m, int64_t ny, int64_t nx, cudaStream_t s) {
     const int64_t work = ny * ((nx + 31) / 32);
-    k_vc_step<<<grid_for(work, 8, nullptr), 256, 0, s>>>(u, un, wE, wS, m, ny, nx);
+    k_vc_step<<<grid_for(work, 8, nullptr), 256, 0, s>>>(u, un, wE, wS, m, ny, nx, kF);
     return cudaGetLastError();
 }
 
 cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c, int64_t ny,
                         int64_t nx, const hxc_launch_cfg *cfg, cudaStream_t s) {
     unsigned b = cfg ? cfg->block[0] * cfg->block[1] * cfg->block[2] : 256;
-    k_vc_step_otf<<<grid_for(ny * nx, b, cfg), b, 0, s>>>(u, un, kap, c, ny, nx);
+    k_vc_step_otf<<<grid_for(ny * nx, b, cfg), b, 0, s>>>(u, un, kap, c, ny, nx, kF);
     return cudaGetLastError();
 }
 
@@ -339,7 +356,7 @@ cudaError_t vc_adjoint(const double *lam, double *lam_out, const double *u, cons
                        int64_t nx, bool do_lam, bool do_grad, cudaStream_t s) {
     const int64_t work = ny * ((nx + 31) / 32);
     k_vc_adjoint<<<grid_for(work, 8, nullptr), 256, 0, s>>>(lam, lam_out, u, wE, wS, m, gk,
-                                                          0.5 * c, ny, nx, do_lam, do_grad);
+                                                          0.5 * c, ny, nx, do_lam, do_grad, kF);
     return cudaGetLastError();
 }
 
@@ -347,7 +364,7 @@ cudaError_t vc_adjoint_otf(const double *lam, double *lam_out, const double *u, 
                            double *gk, double c, int64_t ny, int64_t nx, const hxc_launch_cfg *cfg,
                            cudaStream_t s) {
     unsigned b = cfg ? cfg->block[0] * cfg->block[1] * cfg->block[2] : 256;
-    k_vc_adjoint_otf<<<grid_for(ny * nx, b, cfg), b, 0, s>>>(lam, lam_out, u, kap, gk, c, ny, nx);
+    k_vc_adjoint_otf<<<grid_for(ny * nx, b, cfg), b, 0, s>>>(lam, lam_out, u, kap, gk, c, ny, nx, kF);
     return cudaGetLastError();
 }
 
@@ -368,7 +385,7 @@ cudaError_t vc_batch_persistent(const void *probs, int nprob, unsigned *queue, d
     if (e != cudaSuccess) return e;
     const int g = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 4);
     k_vc_batch<<<g, 256, 0, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
-                                  wE, wS, m, steps);
+                                  wE, wS, m, steps, kF);
     return cudaGetLastError();
 }
 
@@ -383,7 +400,7 @@ cudaError_t vc_batch_step(const void *probs, const int64_t *rows, int nprob, int
                           const double *u, double *un, const double *wE, const double *wS,
                           const double *m, cudaStream_t s) {
     k_vc_batch_step<<<grid_for(total_rows, 8, nullptr), 256, 0, s>>>(
-        static_cast<const VcProblem *>(probs), rows, nprob, u, un, wE, wS, m);
+        static_cast<const VcProblem *>(probs), rows, nprob, u, un, wE, wS, m, kF);
     return cudaGetLastError();
 }
 
