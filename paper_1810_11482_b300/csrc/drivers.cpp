@@ -352,6 +352,34 @@ hxc_status issue_snap_kernels(Heat2dRun &R, int64_t k, int64_t step, std::vector
     const hxc_heat2d_cfg &c = *R.cfg;
     const int64_t T = R.tl.count();
     const double *src = R.buf[step % 2];
+    if (fused) {
+        // one launch for every tile on slot 0 (same bits as the per-tile launches)
+        std::vector<FutRef> deps;
+        for (auto &f : prev)
+            if (f) {
+                deps.push_back(f);
+                break;  // in fused mode every tile holds the same future
+            }
+        for (auto &f : ring_free)
+            if (f) deps.push_back(f);
+        void *scratch = nullptr;
+        hxc_status st = R.dev->scratch_get("tile_norm_grid", k::tile_norm_grid_scratch_bytes(T), &scratch);
+        if (st) return st;
+        double *snap = c.host_norms ? R.snap_dev + (k % 2) * T * R.tile_stride : nullptr;
+        double *norms = R.norm_dev + k * T;
+        const int64_t stride = R.tile_stride, ny = c.ny, nx = c.nx, TY = R.tl.TY, TX = R.tl.TX;
+        FutRef f;
+        st = issue_device_op(
+            R.dev, 0, deps,
+            [=](cudaStream_t s) {
+                return k::tile_norm_grid(src, snap, stride, norms, scratch, ny, nx, TY, TX, s);
+            },
+            {}, &f);
+        if (st) return st;
+        R.stats.launch();
+        for (auto &p : prev) p = f;
+        return HXC_OK;
+    }
     for (int64_t t = 0; t < T; t++) {
         std::vector<FutRef> deps;
         if (prev[t]) deps.push_back(prev[t]);
@@ -553,6 +581,10 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             }
             R.host_stage = (double *)e.first;
         }
+    }
+    if (cfg->mode == HXC_MODE_FUSED) {
+        void *p;
+        if ((st = d->scratch_get("tile_norm_grid", k::tile_norm_grid_scratch_bytes(T), &p))) return st;
     }
     for (int64_t t = 0; t < T; t++) {  // scratch of the norm kernels, before any capture
         void *p;

@@ -339,6 +339,84 @@ __global__ void __launch_bounds__(256) k_tile_norm(const double *__restrict__ sr
     }
 }
 
+// All tiles of a tile grid in one launch (blockIdx.y = tile): the same
+// per-tile reduction order as k_tile_norm, so the same bits.  Tile bounds:
+// rows at p*ny/TY, columns at 2*(q*(nx/2)/TX) when nx is even, else q*nx/TX.
+// The snapshot of tile t goes to snap + t*snap_stride (compact ty x tx).
+__global__ void __launch_bounds__(256) k_tile_norm_grid(const double *__restrict__ src,
+                                                        double *__restrict__ snap,
+                                                        int64_t snap_stride, double *norms,
+                                                        double *partials, unsigned *counters,
+                                                        int64_t ny, int64_t nx, int64_t TY,
+                                                        int64_t TX) {
+    const int g = blockIdx.x;
+    const int64_t tile = blockIdx.y, p = tile / TX, q = tile % TX;
+    const int64_t y0 = p * ny / TY, y1 = (p + 1) * ny / TY;
+    int64_t x0, x1;
+    if (nx % 2 == 0) {
+        x0 = (q * (nx / 2) / TX) * 2;
+        x1 = q + 1 == TX ? nx : ((q + 1) * (nx / 2) / TX) * 2;
+    } else {
+        x0 = q * nx / TX;
+        x1 = (q + 1) * nx / TX;
+    }
+    const int64_t ty = y1 - y0, tx = x1 - x0;
+    double *part = partials + tile * kNormBands;
+    unsigned *counter = counters + tile;
+    double *sn = snap ? snap + tile * snap_stride : nullptr;
+    const int64_t r0 = (int64_t)g * ty / kNormBands, r1 = (int64_t)(g + 1) * ty / kNormBands;
+    const int64_t m = (r1 - r0) * tx;
+    double acc = 0.0;
+    if (tx > 0) {
+        int64_t i = r0 + threadIdx.x / tx, j = threadIdx.x % tx;
+        for (int64_t k = threadIdx.x; k < m; k += 256) {
+            const double v = __ldg(src + (y0 + i) * nx + x0 + j);
+            if (sn) sn[i * tx + j] = v;
+            acc = __fma_rn(v, v, acc);
+            j += 256;
+            if (j >= tx) {
+                i += j / tx;
+                j %= tx;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    __shared__ double ws[8];
+    __shared__ bool is_last;
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sm = __dadd_rn(__dadd_rn(__dadd_rn(ws[0], ws[1]), __dadd_rn(ws[2], ws[3])),
+                              __dadd_rn(__dadd_rn(ws[4], ws[5]), __dadd_rn(ws[6], ws[7])));
+        part[g] = sm;
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == kNormBands - 1;
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        __threadfence();
+        double sm = 0.0;
+        for (int b = 0; b < kNormBands; b++) sm = __dadd_rn(sm, __ldcg(part + b));
+        norms[tile] = __dsqrt_rn(sm);
+        *counter = 0u;  // leave the scratch ready for the next launch
+    }
+}
+
+cudaError_t tile_norm_grid(const double *src, double *snap, int64_t snap_stride, double *norms,
+                           void *scratch, int64_t ny, int64_t nx, int64_t TY, int64_t TX,
+                           cudaStream_t s) {
+    double *partials = static_cast<double *>(scratch);
+    unsigned *counters = reinterpret_cast<unsigned *>(partials + TY * TX * kNormBands);
+    dim3 grid(kNormBands, (unsigned)(TY * TX));
+    k_tile_norm_grid<<<grid, 256, 0, s>>>(src, snap, snap_stride, norms, partials, counters, ny,
+                                          nx, TY, TX);
+    return cudaGetLastError();
+}
+
+size_t tile_norm_grid_scratch_bytes(int64_t tiles) {
+    return (size_t)tiles * (kNormBands * sizeof(double) + sizeof(unsigned)) + 16;
+}
+
 cudaError_t tile_norm(const double *src, double *snap, double *norms, void *scratch,
                       int64_t ny, int64_t nx, int64_t y0, int64_t x0, int64_t ty, int64_t tx,
                       int64_t index, cudaStream_t s) {

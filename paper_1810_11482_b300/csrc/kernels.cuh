@@ -47,6 +47,14 @@ cudaError_t tile_norm(const double *src, double *snap, double *norms, void *scra
                       int64_t ny, int64_t nx, int64_t y0, int64_t x0, int64_t ty, int64_t tx,
                       int64_t index, cudaStream_t s);
 
+// Snapshot + norms of every tile of a TY x TX tile grid (the split of the
+// whole-run entry points) in one launch; same bits as tile_norm per tile.
+// scratch: tile_norm_grid_scratch_bytes(TY*TX), zero on first use.
+cudaError_t tile_norm_grid(const double *src, double *snap, int64_t snap_stride, double *norms,
+                           void *scratch, int64_t ny, int64_t nx, int64_t TY, int64_t TX,
+                           cudaStream_t s);
+size_t tile_norm_grid_scratch_bytes(int64_t tiles);
+
 // 3D FTCS, FP32, periodic: `steps` (1..4) fused steps per launch.  zchunk
 // <= 0 picks the z-chunk length that fills whole waves.
 cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r, int steps,
