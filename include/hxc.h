@@ -409,6 +409,17 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
                                    const hxc_future *deps, int ndeps, hxc_future *out,
                                    hxc_run_stats *stats);
 
+/* ------------------------------------------------------------ tuning */
+
+/* Launch-shape and work-split knobs of the built-in kernels.  They change
+ * speed only: every value gives bit-identical results.  Keys:
+ *   "heat2d.emul"  share of the 2D stencil's three FP64 additions computed by
+ *                  the integer-pipe IEEE adder instead of the FP64 pipe, in
+ *                  half-additions per point, 0..6 (values are clamped).
+ * Returns HXC_E_INVALID for an unknown key. */
+hxc_status hxc_tune_set(const char *key, int64_t value);
+hxc_status hxc_tune_get(const char *key, int64_t *value);
+
 /* ------------------------------------------- norms without allocation */
 
 /* Largest tile grid (tiles_y * tiles_x) hxc_tile_norms_noalloc accepts. */

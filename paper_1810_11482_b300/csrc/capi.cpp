@@ -791,6 +791,26 @@ bad:
     return HXC_E_INVALID;
 }
 
+// ------------------------------------------------------------------ tuning
+hxc_status hxc_tune_set(const char *key, int64_t value) {
+    if (key && strcmp(key, "heat2d.emul") == 0) {
+        k::set_heat2d_emul((int)value);
+        return HXC_OK;
+    }
+    set_error("hxc_tune_set: unknown key '%s'", key ? key : "(null)");
+    return HXC_E_INVALID;
+}
+
+hxc_status hxc_tune_get(const char *key, int64_t *value) {
+    CHECK_OUT(value);
+    if (key && strcmp(key, "heat2d.emul") == 0) {
+        *value = k::heat2d_emul();
+        return HXC_OK;
+    }
+    set_error("hxc_tune_get: unknown key '%s'", key ? key : "(null)");
+    return HXC_E_INVALID;
+}
+
 // ------------------------------------------------------------------ graphs
 hxc_status hxc_graph_begin(hxc_device dh) {
     Ref<Device> d = dev_from_handle(dh);

@@ -9,9 +9,11 @@
 //   2D: s = (uW + uE) + (uN + uS);   t = fma(-4, u, s); u' = fma(r, t, u)
 // (the additions are issued as fma(a, 1, b), which rounds identically).
 // The neighbour sums are symmetric, so mirrored inputs give mirrored bits.
+#include "fp64_int.cuh"
 #include "kernels.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace hxc {
 namespace k {
@@ -56,6 +58,19 @@ __device__ __forceinline__ double ftcs5(double u, double w, double e, double n, 
                                         double r, double one) {
     double s = addf(addf(w, e, one), addf(n, so, one), one);
     double t = __fma_rn(-4.0, u, s);
+    return __fma_rn(r, t, u);
+}
+
+// The same update with its first EM additions (EM = 0..3, in the order
+// w+e, n+s, outer sum) computed by the integer-pipe adder.  Every EM gives
+// the same bits; the split balances the FP64 pipe against the integer pipe.
+template <int EM>
+__device__ __forceinline__ double ftcs5e(double u, double w, double e, double n, double so,
+                                         double r, double one) {
+    const double h = EM >= 1 ? dadd_int(w, e) : addf(w, e, one);
+    const double v = EM >= 2 ? dadd_int(n, so) : addf(n, so, one);
+    const double s = EM >= 3 ? dadd_int(h, v) : addf(h, v, one);
+    const double t = __fma_rn(-4.0, u, s);
     return __fma_rn(r, t, u);
 }
 
@@ -222,7 +237,7 @@ __device__ __forceinline__ double at2(const double *__restrict__ src, int64_t ny
     return (y >= 0 && y < ny && x >= 0 && x < nx) ? __ldg(src + y * nx + x) : 0.0;
 }
 
-template <int V>
+template <int V, int EA, int EB>
 __global__ void __launch_bounds__(256) k_heat2d(const double *__restrict__ src,
                                                 double *__restrict__ dst, int64_t ny, int64_t nx,
                                                 int64_t y0, int64_t x0, int64_t ty, int64_t tx,
@@ -256,11 +271,11 @@ __global__ void __launch_bounds__(256) k_heat2d(const double *__restrict__ src,
             if (active) {
                 if constexpr (V == 2) {
                     double2 o;
-                    o.x = ftcs5(cur.a, left, cur.b, prv.a, nxt.a, r, one);
-                    o.y = ftcs5(cur.b, cur.a, right, prv.b, nxt.b, r, one);
+                    o.x = ftcs5e<EA>(cur.a, left, cur.b, prv.a, nxt.a, r, one);
+                    o.y = ftcs5e<EB>(cur.b, cur.a, right, prv.b, nxt.b, r, one);
                     *reinterpret_cast<double2 *>(dst + y * nx + xl) = o;
                 } else {
-                    dst[y * nx + xl] = ftcs5(cur.a, left, right, prv.a, nxt.a, r, one);
+                    dst[y * nx + xl] = ftcs5e<EA>(cur.a, left, right, prv.a, nxt.a, r, one);
                 }
             }
             prv = cur;
@@ -268,6 +283,19 @@ __global__ void __launch_bounds__(256) k_heat2d(const double *__restrict__ src,
         }
     }
 }
+
+// Integer-pipe share of the 2D additions in half-additions per point (0..6);
+// HXC_HEAT2D_EMUL overrides the default.  The results do not depend on it.
+static int g_heat2d_emul = -1;
+int heat2d_emul() {
+    if (g_heat2d_emul < 0) {
+        const char *e = getenv("HXC_HEAT2D_EMUL");
+        int v = e ? atoi(e) : kHeat2dEmulDefault;
+        g_heat2d_emul = v < 0 ? 0 : (v > 6 ? 6 : v);
+    }
+    return g_heat2d_emul;
+}
+void set_heat2d_emul(int v) { g_heat2d_emul = v < 0 ? 0 : (v > 6 ? 6 : v); }
 
 cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
@@ -281,10 +309,27 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
     const int64_t nwork = ((tx + 32 * V - 1) / (32 * V)) * ((ty + H - 1) / H);
     unsigned b = block_from(cfg, 256);
     unsigned g = grid_from(cfg, std::min<int64_t>((nwork + b / 32 - 1) / (b / 32), (int64_t)sm_count() * 64));
-    if (vec)
-        k_heat2d<2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0);
-    else
-        k_heat2d<1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0);
+    // integer-pipe share of the additions, in half-additions per point
+    // (0..6: points a and b of a lane take floor/ceil of half of it)
+    const int em = heat2d_emul();
+    if (!vec) {
+        switch (em / 2) {
+            case 0: k_heat2d<1, 0, 0><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+            case 1: k_heat2d<1, 1, 1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+            case 2: k_heat2d<1, 2, 2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+            default: k_heat2d<1, 3, 3><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        }
+        return cudaGetLastError();
+    }
+    switch (em) {
+        case 0: k_heat2d<2, 0, 0><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        case 1: k_heat2d<2, 0, 1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        case 2: k_heat2d<2, 1, 1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        case 3: k_heat2d<2, 1, 2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        case 4: k_heat2d<2, 2, 2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        case 5: k_heat2d<2, 2, 3><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        default: k_heat2d<2, 3, 3><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+    }
     return cudaGetLastError();
 }
 

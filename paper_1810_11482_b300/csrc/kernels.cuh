@@ -39,6 +39,12 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
                    const hxc_launch_cfg *cfg, cudaStream_t s);
 
+// Share of the 2D stencil's additions run on the integer pipe, in
+// half-additions per point (0..6); results are bit-identical for every value.
+constexpr int kHeat2dEmulDefault = 0;
+int heat2d_emul();
+void set_heat2d_emul(int v);
+
 // Snapshot + L2 norm of a tile: snap (optional, compact ty x tx) <- tile of
 // src; norms[index] <- sqrt(sum u^2) in a fixed order.  scratch holds
 // kNormScratchBytes, zero on first use, returned to zero by the kernel;

@@ -200,6 +200,8 @@ _SIGS = {
     "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
                                        ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_tune_set": (c_st, [ctypes.c_char_p, i64]),
+    "hxc_tune_get": (c_st, [ctypes.c_char_p, ctypes.POINTER(i64)]),
     "hxc_tile_norms_noalloc": (c_st, [ctypes.c_void_p, i64, i64, i64, i64, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "hxc_heat2d_run_host": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
@@ -533,3 +535,13 @@ def host_empty(shape, dtype=np.float64):
     if isinstance(shape, int):
         shape = (shape,)
     return np.asarray(_Pinned(shape, np.dtype(dtype)))
+
+
+def tune_set(key, value):
+    check(lib().hxc_tune_set(key.encode(), int(value)), "tune_set")
+
+
+def tune_get(key):
+    v = i64()
+    check(lib().hxc_tune_get(key.encode(), ctypes.byref(v)), "tune_get")
+    return int(v.value)

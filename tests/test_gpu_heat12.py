@@ -281,3 +281,49 @@ def test_heat2d_host_entry_point(dev):
     want = oracle.heat2d(u0, 0.2, 40)
     assert relerr(np.array(out), want) <= TOL
     assert st.h2d_bytes == u0.nbytes and st.d2h_bytes >= u0.nbytes
+
+
+# ------------------------------------------- integer-pipe FP64 additions
+
+def test_heat2d_integer_adder_splits_are_bit_identical(dev):
+    """Every split of the 2D additions between the FP64 pipe and the
+    integer-pipe IEEE adder gives the same bits: on smooth bumps, on random
+    finite doubles spanning the whole exponent range (subnormals, mixed
+    signs, huge magnitudes) and on an odd width (scalar path)."""
+    old = hxc.tune_get("heat2d.emul")
+    try:
+        bits = synth.splitmix64(77, 300 * 258)
+        raw = bits.view(np.float64).reshape(300, 258).copy()
+        raw[~np.isfinite(raw)] = 0.0
+        raw = np.where(np.abs(raw) > 1e300, raw * 1e-10, raw)
+        fields = [synth.bumps2d(256, 320, seed=240, nbumps=6, sigma=0.05), raw,
+                  synth.uniform(241, 97 * 131, lo=-1, hi=1).reshape(97, 131)]
+        for u0 in fields:
+            outs = []
+            for em in range(7):
+                hxc.tune_set("heat2d.emul", em)
+                got, _, _, _ = run2d(dev, u0, (2, 3), 0.2, 7, "fused")
+                outs.append(got)
+            for em in range(1, 7):
+                assert np.array_equal(outs[em].view(np.uint64), outs[0].view(np.uint64)), em
+        want = oracle.heat2d(fields[0], 0.2, 7)
+        assert relerr(outs[0], oracle.heat2d(fields[2], 0.2, 7)) <= TOL
+        hxc.tune_set("heat2d.emul", 6)
+        got, _, _, _ = run2d(dev, fields[0], (2, 3), 0.2, 7, "plain")
+        assert relerr(got, want) <= TOL
+    finally:
+        hxc.tune_set("heat2d.emul", old)
+
+
+def test_heat2d_integer_adder_full_size(dev):
+    old = hxc.tune_get("heat2d.emul")
+    try:
+        u0 = synth.bumps2d(8192, 8192, seed=2)
+        hxc.tune_set("heat2d.emul", 0)
+        a, _, _, _ = run2d(dev, u0, (8, 8), 0.2, 1000, "fused")
+        for em in (3, 5):
+            hxc.tune_set("heat2d.emul", em)
+            b, _, _, _ = run2d(dev, u0, (8, 8), 0.2, 1000, "fused")
+            assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), em
+    finally:
+        hxc.tune_set("heat2d.emul", old)
