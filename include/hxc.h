@@ -416,6 +416,9 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *   "heat2d.emul"  share of the 2D stencil's three FP64 additions computed by
  *                  the integer-pipe IEEE adder instead of the FP64 pipe, in
  *                  half-additions per point, 0..6 (values are clamped).
+ *   "heat2d.rows"  rows each warp of the 2D kernel walks (default 8).
+ *   "heat2d.occupancy"  minimum resident 256-thread CTAs per SM the 2D
+ *                  kernel is compiled for, 4..6 (register budget).
  * Returns HXC_E_INVALID for an unknown key. */
 hxc_status hxc_tune_set(const char *key, int64_t value);
 hxc_status hxc_tune_get(const char *key, int64_t *value);

@@ -797,6 +797,14 @@ hxc_status hxc_tune_set(const char *key, int64_t value) {
         k::set_heat2d_emul((int)value);
         return HXC_OK;
     }
+    if (key && strcmp(key, "heat2d.rows") == 0) {
+        k::set_heat2d_rows((int)value);
+        return HXC_OK;
+    }
+    if (key && strcmp(key, "heat2d.occupancy") == 0) {
+        k::set_heat2d_occupancy((int)value);
+        return HXC_OK;
+    }
     set_error("hxc_tune_set: unknown key '%s'", key ? key : "(null)");
     return HXC_E_INVALID;
 }
@@ -805,6 +813,14 @@ hxc_status hxc_tune_get(const char *key, int64_t *value) {
     CHECK_OUT(value);
     if (key && strcmp(key, "heat2d.emul") == 0) {
         *value = k::heat2d_emul();
+        return HXC_OK;
+    }
+    if (key && strcmp(key, "heat2d.rows") == 0) {
+        *value = k::heat2d_rows();
+        return HXC_OK;
+    }
+    if (key && strcmp(key, "heat2d.occupancy") == 0) {
+        *value = k::heat2d_occupancy();
         return HXC_OK;
     }
     set_error("hxc_tune_get: unknown key '%s'", key ? key : "(null)");

@@ -237,8 +237,8 @@ __device__ __forceinline__ double at2(const double *__restrict__ src, int64_t ny
     return (y >= 0 && y < ny && x >= 0 && x < nx) ? __ldg(src + y * nx + x) : 0.0;
 }
 
-template <int V, int EA, int EB>
-__global__ void __launch_bounds__(256) k_heat2d(const double *__restrict__ src,
+template <int V, int EA, int EB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__ src,
                                                 double *__restrict__ dst, int64_t ny, int64_t nx,
                                                 int64_t y0, int64_t x0, int64_t ty, int64_t tx,
                                                 double r, int H, double one) {
@@ -297,11 +297,19 @@ int heat2d_emul() {
 }
 void set_heat2d_emul(int v) { g_heat2d_emul = v < 0 ? 0 : (v > 6 ? 6 : v); }
 
+// Rows per warp of the 2D kernel and its compiled minimum of resident CTAs
+// per SM (speed only).
+static int g_heat2d_rows = kHeat2dRowsDefault, g_heat2d_occ = kHeat2dOccDefault;
+int heat2d_rows() { return g_heat2d_rows; }
+void set_heat2d_rows(int v) { g_heat2d_rows = v < 1 ? 1 : (v > 4096 ? 4096 : v); }
+int heat2d_occupancy() { return g_heat2d_occ; }
+void set_heat2d_occupancy(int v) { g_heat2d_occ = v < 4 ? 4 : (v > 6 ? 6 : v); }
+
 cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
                    const hxc_launch_cfg *cfg, cudaStream_t s) {
     if (ty <= 0 || tx <= 0) return cudaSuccess;
-    const int H = rows_per_warp > 0 ? rows_per_warp : 32;
+    const int H = rows_per_warp > 0 ? rows_per_warp : heat2d_rows();
     const bool vec = (nx % 2 == 0) && (x0 % 2 == 0) && (tx % 2 == 0) &&
                      (reinterpret_cast<uintptr_t>(src) % 16 == 0) &&
                      (reinterpret_cast<uintptr_t>(dst) % 16 == 0);
@@ -310,26 +318,36 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
     unsigned b = block_from(cfg, 256);
     unsigned g = grid_from(cfg, std::min<int64_t>((nwork + b / 32 - 1) / (b / 32), (int64_t)sm_count() * 64));
     // integer-pipe share of the additions, in half-additions per point
-    // (0..6: points a and b of a lane take floor/ceil of half of it)
-    const int em = heat2d_emul();
+    // (0..6: points a and b of a lane take floor/ceil of half of it), and
+    // the minimum resident CTAs per SM the kernel is compiled for (4..6)
+    const int em = heat2d_emul(), occ = heat2d_occupancy();
+#define HXC_L2D(VV, A, B, M) k_heat2d<VV, A, B, M><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0)
     if (!vec) {
         switch (em / 2) {
-            case 0: k_heat2d<1, 0, 0><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-            case 1: k_heat2d<1, 1, 1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-            case 2: k_heat2d<1, 2, 2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-            default: k_heat2d<1, 3, 3><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+            case 0: HXC_L2D(1, 0, 0, 4); break;
+            case 1: HXC_L2D(1, 1, 1, 4); break;
+            case 2: HXC_L2D(1, 2, 2, 4); break;
+            default: HXC_L2D(1, 3, 3, 4); break;
+        }
+        return cudaGetLastError();
+    }
+    if (em == 0) {
+        switch (occ) {
+            case 5: HXC_L2D(2, 0, 0, 5); break;
+            case 6: HXC_L2D(2, 0, 0, 6); break;
+            default: HXC_L2D(2, 0, 0, 4); break;
         }
         return cudaGetLastError();
     }
     switch (em) {
-        case 0: k_heat2d<2, 0, 0><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-        case 1: k_heat2d<2, 0, 1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-        case 2: k_heat2d<2, 1, 1><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-        case 3: k_heat2d<2, 1, 2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-        case 4: k_heat2d<2, 2, 2><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-        case 5: k_heat2d<2, 2, 3><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
-        default: k_heat2d<2, 3, 3><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0); break;
+        case 1: HXC_L2D(2, 0, 1, 4); break;
+        case 2: HXC_L2D(2, 1, 1, 4); break;
+        case 3: HXC_L2D(2, 1, 2, 4); break;
+        case 4: HXC_L2D(2, 2, 2, 4); break;
+        case 5: HXC_L2D(2, 2, 3, 4); break;
+        default: HXC_L2D(2, 3, 3, 4); break;
     }
+#undef HXC_L2D
     return cudaGetLastError();
 }
 

@@ -44,6 +44,11 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
 constexpr int kHeat2dEmulDefault = 0;
 int heat2d_emul();
 void set_heat2d_emul(int v);
+constexpr int kHeat2dRowsDefault = 8, kHeat2dOccDefault = 4;
+int heat2d_rows();
+void set_heat2d_rows(int v);
+int heat2d_occupancy();
+void set_heat2d_occupancy(int v);
 
 // Snapshot + L2 norm of a tile: snap (optional, compact ty x tx) <- tile of
 // src; norms[index] <- sqrt(sum u^2) in a fixed order.  scratch holds

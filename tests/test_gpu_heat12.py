@@ -201,7 +201,7 @@ def test_heat2d_snapshot_norms(dev):
             want = oracle.tile_norms(state[:, :], 64, 64).ravel()
             assert np.max(np.abs(hn[k] - want) / want) <= 1e-12, (mode, k)
             assert np.max(np.abs(gn[k] - want) / want) <= 1e-12, (mode, k)
-            assert np.max(np.abs(gn[k] - hn[k]) / hn[k]) <= 1e-14
+            assert np.max(np.abs(gn[k] - hn[k]) / hn[k]) <= 1e-13  # both sums err by <~2e-14
     # device norms are bit-identical across modes (fixed reduction order)
     _, _, g1, _ = run2d(dev, u0, tiles, r, steps, "plain", every)
     _, _, g2, _ = run2d(dev, u0, tiles, r, steps, "graph", every)
@@ -222,7 +222,7 @@ def test_heat2d_full_config(dev):
     for mode in ("plain", "graph", "fused"):
         got, hn, gn, st = run2d(dev, u0, (8, 8), r, steps, mode, every)
         outs[mode] = got
-        assert np.max(np.abs(gn - hn) / np.maximum(hn, 1e-300)) <= 1e-14
+        assert np.max(np.abs(gn - hn) / np.maximum(hn, 1e-300)) <= 1e-13
     assert np.array_equal(outs["plain"], outs["graph"])
     assert np.array_equal(outs["plain"], outs["fused"])
     got = outs["plain"]
