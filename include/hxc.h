@@ -411,17 +411,28 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
 
 /* ------------------------------------------------------------ tuning */
 
-/* Launch-shape and work-split knobs of the built-in kernels.  They change
- * speed only: every value gives bit-identical results.  Keys:
+/* Launch-shape and work-split knobs of the built-in kernels (the
+ * autotuner's parameters).  They change speed only: every value gives
+ * bit-identical results.  Values are clamped to their ranges.  Keys:
  *   "heat2d.emul"  share of the 2D stencil's three FP64 additions computed by
  *                  the integer-pipe IEEE adder instead of the FP64 pipe, in
- *                  half-additions per point, 0..6 (values are clamped).
+ *                  half-additions per point, 0..6 (default 0).
  *   "heat2d.rows"  rows each warp of the 2D kernel walks (default 8).
  *   "heat2d.occupancy"  minimum resident 256-thread CTAs per SM the 2D
- *                  kernel is compiled for, 4..6 (register budget).
+ *                  kernel is compiled for, 4..6 (default 4).
+ *   "heat3d.zchunks"  z chunks of a 3D launch, 0 = fill whole waves.
+ *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
+ *                  kernel, 0 = SMs / partitions.
+ *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).
  * Returns HXC_E_INVALID for an unknown key. */
 hxc_status hxc_tune_set(const char *key, int64_t value);
 hxc_status hxc_tune_get(const char *key, int64_t *value);
+/* Loads a tuning cache written by the autotuner: a JSON object
+ * {"sm_<major><minor>": {"key": integer, ...}, ...} (the entry of the given
+ * architecture is applied; unknown keys are ignored).  The first
+ * hxc_get_all_devices call loads HXC_TUNE_CACHE, or tune_cache.json next to
+ * the library, automatically. */
+hxc_status hxc_tune_load(const char *path, int major, int minor);
 
 /* ------------------------------------------- norms without allocation */
 

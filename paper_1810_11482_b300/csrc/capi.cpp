@@ -5,6 +5,7 @@
 
 #include "kernels.cuh"
 #include "runtime.hpp"
+#include "tune.hpp"
 
 using namespace hxc;
 
@@ -64,7 +65,11 @@ hxc_status hxc_get_all_devices(int min_major, int min_minor, hxc_device *out, in
         return HXC_E_NODEV;
     }
     std::lock_guard<std::mutex> g(g_dev_m);
-    if (g_devs.empty()) g_devs.assign(count, nullptr);
+    if (g_devs.empty()) {
+        g_devs.assign(count, nullptr);
+        cudaDeviceProp p0;
+        if (cudaGetDeviceProperties(&p0, 0) == cudaSuccess) tune::load_default(p0.major, p0.minor);
+    }
     int found = 0;
     for (int i = 0; i < count; i++) {
         if (!g_devs[i]) {
@@ -793,38 +798,29 @@ bad:
 
 // ------------------------------------------------------------------ tuning
 hxc_status hxc_tune_set(const char *key, int64_t value) {
-    if (key && strcmp(key, "heat2d.emul") == 0) {
-        k::set_heat2d_emul((int)value);
-        return HXC_OK;
+    if (!tune::set(key, value)) {
+        set_error("hxc_tune_set: unknown key '%s'", key ? key : "(null)");
+        return HXC_E_INVALID;
     }
-    if (key && strcmp(key, "heat2d.rows") == 0) {
-        k::set_heat2d_rows((int)value);
-        return HXC_OK;
-    }
-    if (key && strcmp(key, "heat2d.occupancy") == 0) {
-        k::set_heat2d_occupancy((int)value);
-        return HXC_OK;
-    }
-    set_error("hxc_tune_set: unknown key '%s'", key ? key : "(null)");
-    return HXC_E_INVALID;
+    return HXC_OK;
 }
 
 hxc_status hxc_tune_get(const char *key, int64_t *value) {
     CHECK_OUT(value);
-    if (key && strcmp(key, "heat2d.emul") == 0) {
-        *value = k::heat2d_emul();
-        return HXC_OK;
+    if (!tune::known(key)) {
+        set_error("hxc_tune_get: unknown key '%s'", key ? key : "(null)");
+        return HXC_E_INVALID;
     }
-    if (key && strcmp(key, "heat2d.rows") == 0) {
-        *value = k::heat2d_rows();
-        return HXC_OK;
+    *value = tune::get(key);
+    return HXC_OK;
+}
+
+hxc_status hxc_tune_load(const char *path, int major, int minor) {
+    if (!path) {
+        set_error("hxc_tune_load: NULL path");
+        return HXC_E_INVALID;
     }
-    if (key && strcmp(key, "heat2d.occupancy") == 0) {
-        *value = k::heat2d_occupancy();
-        return HXC_OK;
-    }
-    set_error("hxc_tune_get: unknown key '%s'", key ? key : "(null)");
-    return HXC_E_INVALID;
+    return tune::load_file(path, major, minor);
 }
 
 // ------------------------------------------------------------------ graphs

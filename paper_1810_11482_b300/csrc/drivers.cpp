@@ -15,6 +15,7 @@
 
 #include "drivers_util.hpp"
 #include "kernels.cuh"
+#include "tune.hpp"
 #include "runtime.hpp"
 
 using namespace hxc;
@@ -87,7 +88,8 @@ hxc_status issue_heat1d(const Heat1dPlan &pl, int steps, int T, int &flip, std::
             const hxc_launch_cfg *pc = nullptr;
             if (t > 1) {
                 // spread the SMs over the partitions that run concurrently
-                int g = std::max(1, k::sm_count() / parts);
+                const int64_t tc = tune::get("heat1d.tb_ctas");
+                int g = tc > 0 ? (int)tc : std::max(1, k::sm_count() / parts);
                 cfg = hxc_launch_cfg{{(uint32_t)g, 1, 1}, {512, 1, 1}};
                 pc = &cfg;
             }

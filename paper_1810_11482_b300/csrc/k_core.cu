@@ -11,6 +11,7 @@
 // The neighbour sums are symmetric, so mirrored inputs give mirrored bits.
 #include "fp64_int.cuh"
 #include "kernels.cuh"
+#include "tune.hpp"
 
 #include <algorithm>
 #include <cstdlib>
@@ -284,26 +285,13 @@ __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__
     }
 }
 
-// Integer-pipe share of the 2D additions in half-additions per point (0..6);
-// HXC_HEAT2D_EMUL overrides the default.  The results do not depend on it.
-static int g_heat2d_emul = -1;
-int heat2d_emul() {
-    if (g_heat2d_emul < 0) {
-        const char *e = getenv("HXC_HEAT2D_EMUL");
-        int v = e ? atoi(e) : kHeat2dEmulDefault;
-        g_heat2d_emul = v < 0 ? 0 : (v > 6 ? 6 : v);
-    }
-    return g_heat2d_emul;
-}
-void set_heat2d_emul(int v) { g_heat2d_emul = v < 0 ? 0 : (v > 6 ? 6 : v); }
-
-// Rows per warp of the 2D kernel and its compiled minimum of resident CTAs
-// per SM (speed only).
-static int g_heat2d_rows = kHeat2dRowsDefault, g_heat2d_occ = kHeat2dOccDefault;
-int heat2d_rows() { return g_heat2d_rows; }
-void set_heat2d_rows(int v) { g_heat2d_rows = v < 1 ? 1 : (v > 4096 ? 4096 : v); }
-int heat2d_occupancy() { return g_heat2d_occ; }
-void set_heat2d_occupancy(int v) { g_heat2d_occ = v < 4 ? 4 : (v > 6 ? 6 : v); }
+// 2D knobs live in the tuning registry (speed only, never results).
+int heat2d_emul() { return (int)tune::get("heat2d.emul"); }
+void set_heat2d_emul(int v) { tune::set("heat2d.emul", v); }
+int heat2d_rows() { return (int)tune::get("heat2d.rows"); }
+void set_heat2d_rows(int v) { tune::set("heat2d.rows", v); }
+int heat2d_occupancy() { return (int)tune::get("heat2d.occupancy"); }
+void set_heat2d_occupancy(int v) { tune::set("heat2d.occupancy", v); }
 
 cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,

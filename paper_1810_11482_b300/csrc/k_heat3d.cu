@@ -18,6 +18,7 @@
 // distance t of the region edge are wrong at level t and are never written:
 // only the central (RX-2T) x (RY-2T) columns of level T are stored.
 #include "kernels.cuh"
+#include "tune.hpp"
 
 namespace hxc {
 namespace k {
@@ -174,7 +175,10 @@ int heat3d_default_zchunk(int nz, int ny, int nx, int T) {
 cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r, int steps,
                    int zchunk, const hxc_launch_cfg *cfg, cudaStream_t s) {
     if (steps < 1 || steps > 4) return cudaErrorInvalidValue;
-    if (zchunk <= 0) zchunk = heat3d_default_zchunk(nz, ny, nx, steps);
+    if (zchunk <= 0) {
+        const int nch = (int)tune::get("heat3d.zchunks");
+        zchunk = nch > 0 ? (nz + nch - 1) / nch : heat3d_default_zchunk(nz, ny, nx, steps);
+    }
     const int blocks = heat3d_blocks(nz, ny, nx, steps, zchunk);
     unsigned g = cfg ? cfg->grid[0] * cfg->grid[1] * cfg->grid[2] : (unsigned)blocks;
     if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != NT) return cudaErrorInvalidValue;

@@ -24,6 +24,7 @@
 //   gk_a = fma(c/2, S, gk_a)
 // i.e. dL/dkappa_a = sum_f dk_f/dkappa_a * c (u_b - u_a)(l_a - l_b).
 #include "kernels.cuh"
+#include "tune.hpp"
 
 #include <algorithm>
 
@@ -383,7 +384,7 @@ cudaError_t vc_batch_persistent(const void *probs, int nprob, unsigned *queue, d
                                 int steps, int ctas_per_sm, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const int g = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : 4);
+    const int g = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : (int)tune::get("batch.ctas_per_sm"));
     k_vc_batch<<<g, 256, 0, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
                                   wE, wS, m, steps, kF);
     return cudaGetLastError();

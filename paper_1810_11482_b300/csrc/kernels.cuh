@@ -39,12 +39,11 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
                    const hxc_launch_cfg *cfg, cudaStream_t s);
 
-// Share of the 2D stencil's additions run on the integer pipe, in
-// half-additions per point (0..6); results are bit-identical for every value.
-constexpr int kHeat2dEmulDefault = 0;
+// 2D kernel knobs (tuning registry): share of the additions run on the
+// integer pipe (half-additions per point, 0..6), rows per warp, compiled
+// occupancy.  Results are bit-identical for every value.
 int heat2d_emul();
 void set_heat2d_emul(int v);
-constexpr int kHeat2dRowsDefault = 8, kHeat2dOccDefault = 4;
 int heat2d_rows();
 void set_heat2d_rows(int v);
 int heat2d_occupancy();

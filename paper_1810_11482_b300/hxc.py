@@ -202,6 +202,7 @@ _SIGS = {
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
     "hxc_tune_set": (c_st, [ctypes.c_char_p, i64]),
     "hxc_tune_get": (c_st, [ctypes.c_char_p, ctypes.POINTER(i64)]),
+    "hxc_tune_load": (c_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int]),
     "hxc_tile_norms_noalloc": (c_st, [ctypes.c_void_p, i64, i64, i64, i64, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "hxc_heat2d_run_host": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
@@ -545,3 +546,7 @@ def tune_get(key):
     v = i64()
     check(lib().hxc_tune_get(key.encode(), ctypes.byref(v)), "tune_get")
     return int(v.value)
+
+
+def tune_load(path, major=10, minor=3):
+    check(lib().hxc_tune_load(str(path).encode(), major, minor), "tune_load")

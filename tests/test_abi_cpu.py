@@ -190,3 +190,31 @@ def test_get_all_devices_without_gpu(L):
     n = ctypes.c_int(-1)
     assert L.hxc_get_all_devices(2, 0, None, 0, ctypes.byref(n)) == hxc.HXC_E_NODEV
     assert n.value == 0
+
+
+def test_tuning_registry_and_cache(L, tmp_path):
+    old = hxc.tune_get("heat2d.rows")
+    try:
+        hxc.tune_set("heat2d.rows", 16)
+        assert hxc.tune_get("heat2d.rows") == 16
+        hxc.tune_set("heat2d.occupancy", 99)  # clamped to the range 4..6
+        assert hxc.tune_get("heat2d.occupancy") == 6
+        with pytest.raises(hxc.HxcError):
+            hxc.tune_set("no.such.knob", 1)
+        nested = tmp_path / "t.json"
+        nested.write_text('{"sm_90": {"heat2d.rows": 3}, "sm_103": {"heat2d.rows": 64, '
+                          '"batch.ctas_per_sm": 6, "future.knob": 1}}')
+        hxc.tune_load(nested, 10, 3)
+        assert hxc.tune_get("heat2d.rows") == 64 and hxc.tune_get("batch.ctas_per_sm") == 6
+        flat = tmp_path / "f.json"
+        flat.write_text('{"heat2d.rows": 24}')
+        hxc.tune_load(flat, 10, 3)
+        assert hxc.tune_get("heat2d.rows") == 24
+        bad = tmp_path / "b.json"
+        bad.write_text('{"heat2d.rows": }')
+        with pytest.raises(hxc.HxcError):
+            hxc.tune_load(bad, 10, 3)
+    finally:
+        hxc.tune_set("heat2d.rows", old)
+        hxc.tune_set("heat2d.occupancy", 4)
+        hxc.tune_set("batch.ctas_per_sm", 4)
