@@ -110,14 +110,16 @@ def tune(quick=False, log=print):
     result.update(_search(timer, {"heat1d.tb_ctas": [0, 8, 12, 16, 18, 24, 32]},
                           lambda d: hxc.heat1d_run(dev, p, q, n1, 8, 0.25, 100, "fused", 0, d)[0],
                           log))
-    # batch: CTAs per SM of the persistent kernel (a reduced batch)
-    sides, offs, kap, ub, cs = synth.batch_input(nprob=256 if quick else 1024, seed=4)
+    # batch: CTAs per SM of the persistent kernel, on the full batch (its
+    # largest problems set the critical path of the
+    # persistent kernel, so a subset would tune for a different balance)
+    sides, offs, kap, ub, cs = synth.batch_input(nprob=256 if quick else 4096, seed=4)
     bu, bk = dev.buffer(ub.nbytes), dev.buffer(kap.nbytes)
     bu.write(ub).get()
     bk.write(kap).get()
     log("batch")
-    result.update(_search(timer, {"batch.ctas_per_sm": [2, 4, 6, 8]},
-                          lambda d: hxc.varcoef_batch_run(dev, bu, bk, sides, cs, 10, "fused", d)[0],
+    result.update(_search(timer, {"batch.ctas_per_sm": [1, 2, 3, 4]},
+                          lambda d: hxc.varcoef_batch_run(dev, bu, bk, sides, cs, 50, "fused", d)[0],
                           log))
     return dev, result
 

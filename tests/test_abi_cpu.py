@@ -218,3 +218,15 @@ def test_tuning_registry_and_cache(L, tmp_path):
         hxc.tune_set("heat2d.rows", old)
         hxc.tune_set("heat2d.occupancy", 4)
         hxc.tune_set("batch.ctas_per_sm", 4)
+
+
+def test_shipped_tuning_cache_parses(L):
+    import json
+    path = os.path.join(ROOT, "paper_1810_11482_b300", "tune_cache.json")
+    data = json.load(open(path))
+    assert "sm_103" in data and set(data["sm_103"]) <= {"heat2d.emul", "heat2d.rows",
+                                                        "heat2d.occupancy", "heat3d.zchunks",
+                                                        "heat1d.tb_ctas", "batch.ctas_per_sm"}
+    hxc.tune_load(path, 10, 3)
+    for k, v in data["sm_103"].items():
+        assert hxc.tune_get(k) == v
