@@ -270,6 +270,44 @@ hxc_status hxc_launch(hxc_device dev, hxc_kernel_id id, const void *args, size_t
                       const hxc_launch_cfg *cfg, int slot, const hxc_future *deps, int ndeps,
                       hxc_future *out);
 
+/* ---------------------------------------------------- run-time programs */
+
+/* Sec. 4 "program" and Listing 2: user CUDA source compiled at run time
+ * (NVRTC) for the device's architecture.  Creation reads the source
+ * synchronously; hxc_program_build returns a future (Listing 2 adds it to
+ * the futures it waits for); hxc_program_run launches a kernel of the
+ * program with buffers (and values) as arguments and an explicit grid and
+ * block (Listing 2, "run(args, name, grid, block)"), returning a future.
+ * Every run of a program depends on the program's last build. */
+typedef struct hxc_program_t *hxc_program;
+
+/* A kernel argument: a buffer (passed as its device pointer) or, when buf is
+ * NULL, `size` bytes at `value` (copied when hxc_program_run is called). */
+typedef struct {
+    hxc_buffer buf;
+    const void *value;
+    size_t size;
+} hxc_kernel_arg;
+
+hxc_status hxc_program_create_with_source(hxc_device dev, const char *source, const char *name,
+                                          hxc_program *out);
+/* Listing 2 "create_program_with_file". */
+hxc_status hxc_program_create_with_file(hxc_device dev, const char *path, hxc_program *out);
+/* Compiles the program and loads the kernels named in the comma-separated
+ * list kernel_names (name expressions: plain names for extern "C" kernels,
+ * C++ names otherwise).  `options` (may be NULL) are extra NVRTC options
+ * separated by spaces.  The future holds HXC_E_INVALID on a compile error
+ * (see hxc_program_build_log), HXC_E_UNSUPPORTED if NVRTC is unavailable. */
+hxc_status hxc_program_build(hxc_program prog, const char *kernel_names, const char *options,
+                             const hxc_future *deps, int ndeps, hxc_future *out);
+/* Compiler output of the last build: copies up to cap-1 bytes and a NUL;
+ * *len receives the full length. */
+hxc_status hxc_program_build_log(hxc_program prog, char *buf, size_t cap, size_t *len);
+hxc_status hxc_program_run(hxc_program prog, const char *kernel_name, const hxc_kernel_arg *args,
+                           int nargs, const hxc_launch_cfg *cfg, int slot, const hxc_future *deps,
+                           int ndeps, hxc_future *out);
+hxc_status hxc_program_release(hxc_program prog);
+
 /* ------------------------------------------------------------------ graphs */
 
 /* Captures every operation subsequently issued to `dev` by this thread into

@@ -51,7 +51,7 @@ c_st = ctypes.c_int
 i64 = ctypes.c_int64
 HOST_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
 # argument structs beyond the core set, checked against the header by the tests
-EXTRA_STRUCTS = ["hxc_heat3d_args", "hxc_varcoef2d_args", "hxc_adjoint2d_args"]
+EXTRA_STRUCTS = ["hxc_heat3d_args", "hxc_varcoef2d_args", "hxc_adjoint2d_args", "hxc_kernel_arg"]
 
 
 class hxc_launch_cfg(ctypes.Structure):
@@ -98,6 +98,10 @@ class hxc_adjoint2d_args(ctypes.Structure):
 
 class hxc_partition_args(ctypes.Structure):
     _fields_ = [("out", c_buf), ("n", i64), ("offset", i64)]
+
+
+class hxc_kernel_arg(ctypes.Structure):
+    _fields_ = [("buf", c_buf), ("value", ctypes.c_void_p), ("size", ctypes.c_size_t)]
 
 
 class hxc_run_stats(ctypes.Structure):
@@ -200,6 +204,17 @@ _SIGS = {
     "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
                                        ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_program_create_with_source": (c_st, [c_dev, ctypes.c_char_p, ctypes.c_char_p,
+                                              ctypes.POINTER(ctypes.c_void_p)]),
+    "hxc_program_create_with_file": (c_st, [c_dev, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "hxc_program_build": (c_st, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p,
+                                 ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut)]),
+    "hxc_program_build_log": (c_st, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "hxc_program_run": (c_st, [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(hxc_kernel_arg),
+                               ctypes.c_int, ctypes.POINTER(hxc_launch_cfg), ctypes.c_int,
+                               ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut)]),
+    "hxc_program_release": (c_st, [ctypes.c_void_p]),
     "hxc_tune_set": (c_st, [ctypes.c_char_p, i64]),
     "hxc_tune_get": (c_st, [ctypes.c_char_p, ctypes.POINTER(i64)]),
     "hxc_tune_load": (c_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int]),
@@ -550,3 +565,68 @@ def tune_get(key):
 
 def tune_load(path, major=10, minor=3):
     check(lib().hxc_tune_load(str(path).encode(), major, minor), "tune_load")
+
+
+class Program:
+    """A run-time compiled program (the paper's `program`)."""
+
+    def __init__(self, h):
+        self.h = h
+
+    @staticmethod
+    def from_file(dev, path):
+        out = ctypes.c_void_p()
+        check(lib().hxc_program_create_with_file(dev.h, str(path).encode(), ctypes.byref(out)),
+              "create_program_with_file")
+        return Program(out.value)
+
+    @staticmethod
+    def from_source(dev, source, name="program.cu"):
+        out = ctypes.c_void_p()
+        check(lib().hxc_program_create_with_source(dev.h, source.encode(), name.encode(),
+                                                   ctypes.byref(out)), "create_program")
+        return Program(out.value)
+
+    def build(self, kernel_names, options=None, deps=()):
+        arr, n = _futs(deps)
+        out = c_fut()
+        check(lib().hxc_program_build(self.h, kernel_names.encode(),
+                                      options.encode() if options else None, arr, n,
+                                      ctypes.byref(out)), "build")
+        return Future(out.value)
+
+    def log(self):
+        n = ctypes.c_size_t()
+        check(lib().hxc_program_build_log(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        check(lib().hxc_program_build_log(self.h, buf, n.value + 1, None))
+        return buf.value.decode(errors="replace")
+
+    def run(self, name, args, grid, block, slot=0, deps=()):
+        """args: Buffer objects or (ctypes scalar) values."""
+        arr = (hxc_kernel_arg * max(1, len(args)))()
+        keep = []
+        for i, a in enumerate(args):
+            if isinstance(a, Buffer):
+                arr[i].buf = a.h
+            else:
+                keep.append(a)
+                arr[i].value = ctypes.cast(ctypes.pointer(a), ctypes.c_void_p)
+                arr[i].size = ctypes.sizeof(a)
+        cfg = hxc_launch_cfg(tuple(grid), tuple(block))
+        darr, n = _futs(deps)
+        out = c_fut()
+        check(lib().hxc_program_run(self.h, name.encode(), arr, len(args), ctypes.byref(cfg), slot,
+                                    darr, n, ctypes.byref(out)), "run")
+        return Future(out.value)
+
+    def close(self):
+        if self.h:
+            lib().hxc_program_release(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

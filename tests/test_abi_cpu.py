@@ -230,3 +230,13 @@ def test_shipped_tuning_cache_parses(L):
     hxc.tune_load(path, 10, 3)
     for k, v in data["sm_103"].items():
         assert hxc.tune_get(k) == v
+
+
+def test_program_calls_reject_bad_handles():
+    L = hxc.lib()
+    out = ctypes.c_void_p()
+    assert L.hxc_program_create_with_source(None, b"x", b"x.cu", ctypes.byref(out)) == hxc.HXC_E_INVALID
+    assert L.hxc_program_create_with_file(None, b"/nonexistent/x.cu", ctypes.byref(out)) == hxc.HXC_E_INVALID
+    n = ctypes.c_size_t()
+    assert L.hxc_program_build_log(None, None, 0, ctypes.byref(n)) == hxc.HXC_E_INVALID
+    assert L.hxc_program_release(None) == hxc.HXC_E_INVALID
