@@ -223,7 +223,8 @@ typedef enum {
     HXC_K_VARCOEF2D = 7,
     /* Adjoint step with kappa-gradient accumulation. */
     HXC_K_ADJOINT2D = 8,
-    /* Sec. 5.1.2 partition kernel: out_i = sqrt(sin(i)^2 + cos(i)^2). */
+    /* Sec. 5.1.2 partition kernel k, in place on x[offset, offset+n):
+     * x_i <- sqrt(sin(x_i)^2 + cos(x_i)^2), 1 up to rounding. */
     HXC_K_PARTITION = 9
 } hxc_kernel_id;
 
@@ -262,13 +263,35 @@ typedef struct {
     int64_t ny, nx;
     double c;
 } hxc_adjoint2d_args;
-typedef struct { hxc_buffer out; int64_t n, offset; } hxc_partition_args;
+typedef struct { hxc_buffer x; int64_t n, offset; } hxc_partition_args;
 
 /* Launches kernel `id` with the argument struct `args` (of size args_size,
  * which must equal the struct's size) on stream slot `slot` after deps. */
 hxc_status hxc_launch(hxc_device dev, hxc_kernel_id id, const void *args, size_t args_size,
                       const hxc_launch_cfg *cfg, int slot, const hxc_future *deps, int ndeps,
                       hxc_future *out);
+
+/* ----------------------------------------- partition benchmark (Alg. 1) */
+
+/* Sec. 5.1.2, Algorithm 1: the n doubles at host_x are split into `parts`
+ * contiguous partitions (partition i holds [i*n/parts, (i+1)*n/parts)) and
+ * issued as three loops over the partitions: partition i is written into
+ * `work` (at least 8n bytes, same offsets) on stream slot i, the partition
+ * kernel (HXC_K_PARTITION) runs on it after its write, and it is read back
+ * into host_r after its kernel -- each operation a future of the public
+ * calls.  host_r may equal host_x; both should be page-locked
+ * (hxc_host_alloc) for the copies to overlap with the kernels.  The first
+ * writes wait for deps.  *out completes when every partition is on the host
+ * (with deps alone when n = 0).  1 <= parts <= 64. */
+hxc_status hxc_partition_run(hxc_device dev, const double *host_x, double *host_r, int64_t n,
+                             int parts, hxc_buffer work, const hxc_future *deps, int ndeps,
+                             hxc_future *out);
+/* The same three loops as plain CUDA runtime calls (cudaMemcpyAsync, kernel,
+ * cudaMemcpyAsync) on the same stream slots, without futures, then a
+ * synchronisation of each stream: the native comparison of Sec. 5.1.2.
+ * Returns when the results are on the host. */
+hxc_status hxc_partition_run_native(hxc_device dev, const double *host_x, double *host_r,
+                                    int64_t n, int parts, hxc_buffer work);
 
 /* ---------------------------------------------------- run-time programs */
 

@@ -77,6 +77,13 @@ def sum_u32(x):
     return int(lib().ora_sum_u32(x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), x.size))
 
 
+def partition_k(x):
+    """Sec. 5.1.2: the partition kernel k(x) = sqrt(sin(x)^2 + cos(x)^2),
+    elementwise, with the C library's sin, cos and sqrt."""
+    x = _f64(x)
+    return np.sqrt(np.sin(x) ** 2 + np.cos(x) ** 2)
+
+
 def heat1d(u0, r, steps):
     """Periodic 1D FTCS: u'_j = u_j + r (u_{j-1} - 2 u_j + u_{j+1})."""
     u0 = _f64(u0)

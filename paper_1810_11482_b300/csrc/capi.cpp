@@ -655,10 +655,10 @@ hxc_status hxc_launch(hxc_device dh, hxc_kernel_id id, const void *args, size_t 
         case HXC_K_PARTITION: {
             ARGS(hxc_partition_args);
             if (a.n < 0 || a.offset < 0 || !cfg_ok(pc, 32, 1024)) goto bad;
-            BUF(o, a.out, (size_t)a.n * 8, "partition.out");
-            double *optr = (double *)o->ptr;
-            int64_t n = a.n, off = a.offset;
-            op = [=](cudaStream_t s) { return k::partition(optr, n, off, pc ? &cfg : nullptr, s); };
+            BUF(o, a.x, (size_t)(a.offset + a.n) * 8, "partition.x");
+            double *xptr = (double *)o->ptr + a.offset;
+            int64_t n = a.n;
+            op = [=](cudaStream_t s) { return k::partition(xptr, n, pc ? &cfg : nullptr, s); };
             break;
         }
         case HXC_K_HEAT1D: {

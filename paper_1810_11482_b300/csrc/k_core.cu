@@ -110,19 +110,20 @@ cudaError_t prk(const double *in, double *out, int64_t n, const hxc_launch_cfg *
 }
 
 // ------------------------------------------------- Sec. 5.1.2 partition k
-__global__ void k_partition(double *__restrict__ out, int64_t n, int64_t offset) {
+// In place: x_i <- sqrt(sin(x_i)^2 + cos(x_i)^2), one sincos per element.
+__global__ void k_partition(double *__restrict__ x, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double x = (double)(offset + i);
-        double sv = sin(x), cv = cos(x);
-        out[i] = sqrt(sv * sv + cv * cv);
+        double sv, cv;
+        sincos(x[i], &sv, &cv);
+        x[i] = sqrt(sv * sv + cv * cv);
     }
 }
 
-cudaError_t partition(double *out, int64_t n, int64_t offset, const hxc_launch_cfg *cfg,
-                      cudaStream_t s) {
+cudaError_t partition(double *x, int64_t n, const hxc_launch_cfg *cfg, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
     unsigned b = block_from(cfg, 256), g = grid_from(cfg, std::min<int64_t>((n + b - 1) / b, sm_count() * 8));
-    k_partition<<<g, b, 0, s>>>(out, n, offset);
+    k_partition<<<g, b, 0, s>>>(x, n);
     return cudaGetLastError();
 }
 

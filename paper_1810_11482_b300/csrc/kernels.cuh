@@ -24,8 +24,7 @@ cudaError_t sum_u32(const uint32_t *in, unsigned long long *result, int64_t n,
                     const hxc_launch_cfg *cfg, cudaStream_t s);
 cudaError_t prk(const double *in, double *out, int64_t n, const hxc_launch_cfg *cfg,
                 cudaStream_t s);
-cudaError_t partition(double *out, int64_t n, int64_t offset, const hxc_launch_cfg *cfg,
-                      cudaStream_t s);
+cudaError_t partition(double *x, int64_t n, const hxc_launch_cfg *cfg, cudaStream_t s);
 
 // dst[lo, lo+count) <- `steps` periodic FTCS steps of src (period n).
 cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,

@@ -97,7 +97,7 @@ class hxc_adjoint2d_args(ctypes.Structure):
 
 
 class hxc_partition_args(ctypes.Structure):
-    _fields_ = [("out", c_buf), ("n", i64), ("offset", i64)]
+    _fields_ = [("x", c_buf), ("n", i64), ("offset", i64)]
 
 
 class hxc_kernel_arg(ctypes.Structure):
@@ -204,6 +204,10 @@ _SIGS = {
     "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
                                        ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_partition_run": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, ctypes.c_int, c_buf,
+                                 ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut)]),
+    "hxc_partition_run_native": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, ctypes.c_int,
+                                        c_buf]),
     "hxc_program_create_with_source": (c_st, [c_dev, ctypes.c_char_p, ctypes.c_char_p,
                                               ctypes.POINTER(ctypes.c_void_p)]),
     "hxc_program_create_with_file": (c_st, [c_dev, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -565,6 +569,37 @@ def tune_get(key):
 
 def tune_load(path, major=10, minor=3):
     check(lib().hxc_tune_load(str(path).encode(), major, minor), "tune_load")
+
+
+def _f64_host(a, what):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError(what + " must be a C-contiguous float64 array")
+    return a.ctypes.data
+
+
+def partition_run(dev, host_x, host_r, parts, work, deps=()):
+    """Algorithm 1 on the futures layer (hxc_partition_run); returns the
+    future of the last copy back.  host_x/host_r: float64 arrays (pinned
+    ones from host_empty overlap)."""
+    if host_r.size != host_x.size:
+        raise ValueError("host_x and host_r differ in size")
+    arr, n = _futs(deps)
+    out = c_fut()
+    check(lib().hxc_partition_run(dev.h, _f64_host(host_x, "host_x"), _f64_host(host_r, "host_r"),
+                                  host_x.size, parts, work.h, arr, n, ctypes.byref(out)),
+          "partition_run")
+    f = Future(out.value)
+    f._host = (host_x, host_r)
+    return f
+
+
+def partition_run_native(dev, host_x, host_r, parts, work):
+    """The same loops as plain CUDA calls on the same streams; blocks."""
+    if host_r.size != host_x.size:
+        raise ValueError("host_x and host_r differ in size")
+    check(lib().hxc_partition_run_native(dev.h, _f64_host(host_x, "host_x"),
+                                         _f64_host(host_r, "host_r"), host_x.size, parts, work.h),
+          "partition_run_native")
 
 
 class Program:

@@ -162,3 +162,17 @@ def fd_directions(ndir, n_kappa, n_u0, seed=8):
     d = normal(seed, ndir * m).reshape(ndir, m)
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     return d[:, :n_kappa], d[:, n_kappa:]
+
+
+def partition_sizes(ms=range(1, 9), block=256, parts=4):
+    """Vector lengths of the partition benchmark: n = 2^m * 1024 * block * parts."""
+    return [(1 << m) * 1024 * block * parts for m in ms]
+
+
+def partition_input(n, out=None):
+    """The partition benchmark's vector: x_i = i (the kernel's argument is the
+    element's index).  Filled into `out` (e.g. a page-locked array) if given."""
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
+    out[:] = np.arange(n, dtype=np.float64)
+    return out

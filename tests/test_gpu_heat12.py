@@ -75,11 +75,14 @@ def test_prk_stencil_bitexact(dev):
 
 def test_partition_kernel_is_one(dev):
     """Sec. 5.1.2: sqrt(sin^2 i + cos^2 i) = 1 within CUDA's sin/cos/sqrt error bounds."""
-    n = 1 << 20
-    b = dev.buffer(n * 8)
-    dev.launch(hxc.HXC_K_PARTITION, hxc.hxc_partition_args(b.h, n, 12345)).get()
-    out = download(b, n)
-    assert np.max(np.abs(out - 1.0)) <= 8 * np.finfo(np.float64).eps
+    n, off = 1 << 20, 333
+    x = synth.partition_input(n + off) + 12345.0
+    b = upload(dev, x)
+    dev.launch(hxc.HXC_K_PARTITION, hxc.hxc_partition_args(b.h, n, off)).get()
+    out = download(b, n + off)
+    assert np.array_equal(out[:off], x[:off])  # outside [offset, offset+n) untouched
+    assert np.max(np.abs(out[off:] - 1.0)) <= 8 * np.finfo(np.float64).eps
+    assert np.max(np.abs(out[off:] - oracle.partition_k(x[off:]))) <= 8 * np.finfo(np.float64).eps
 
 
 # ------------------------------------------------------------------ 1D

@@ -445,3 +445,19 @@ def test_adjoint_u0_gradient_is_forward_of_residual():
     uT = oracle.varcoef2d(u0, kap, c, steps)
     want = oracle.varcoef2d(2 * (uT - utgt), kap, c, steps)
     assert np.max(np.abs(gu - want)) <= 64 * EPS * np.max(np.abs(want))
+
+
+def test_partition_kernel_is_one_and_sizes():
+    """Sec. 5.1.2: k(x) = sqrt(sin^2 x + cos^2 x) is identically 1 (up to the
+    rounding of sin, cos, the squares, the sum and the root), and the vector
+    lengths are 2^m * 1024 * 256 * 4 for m = 1..8, i.e. 2^21 .. 2^28."""
+    x = np.concatenate([np.arange(4096, dtype=np.float64),
+                        np.arange((1 << 28) - 4096, 1 << 28, dtype=np.float64),
+                        synth.uniform(11, 4096, lo=0.0, hi=float(1 << 28)).round()])
+    k = oracle.partition_k(x)
+    assert np.max(np.abs(k - 1.0)) <= 4 * np.finfo(np.float64).eps
+    assert k[0] == 1.0  # sin 0 = 0, cos 0 = 1 exactly
+    # a sign slip (sin^2 - cos^2 = -cos 2x) or a squared-sum mix-up is far from 1
+    assert np.max(np.abs(np.sqrt(np.abs(np.sin(x) ** 2 - np.cos(x) ** 2)) - 1.0)) > 0.5
+    assert synth.partition_sizes() == [1 << e for e in range(21, 29)]
+    assert np.array_equal(synth.partition_input(5), [0.0, 1.0, 2.0, 3.0, 4.0])
