@@ -400,7 +400,120 @@ def secondary(dev, timer, peaks):
     speedups(res)
     res["gradient_over_forward_time"] = res["fused"]["ms"] / res["forward"]["ms"]
     out["adjoint_2048^2_500steps_f64"] = res
+    del b0, bkr, bkk, tgt, uT, lam, lb, gk, gu
+    out["partition_alg1_p4_f64"] = partition_bench(dev, timer)
+    out["mandelbrot_png_f32"] = mandelbrot_bench(dev, timer)
     return out
+
+
+FP32_LANES_PER_SM = 128  # FP32 operations per SM per clock (an FMA counts as one)
+
+
+def mandelbrot_bench(dev, timer, sides=(1024, 2048, 4096, 8192), max_iter=256, level=1):
+    """Sec. 5.1.3: images of increasing size, each computed on the device,
+    copied back and written as a PNG file (zlib level 1); the whole sequence
+    timed on the host clock with the files written synchronously after each
+    image, and as continuations that overlap the next images.  Plus the
+    kernel alone on the largest image against the FP32 issue rate."""
+    import shutil
+    import tempfile
+    import time
+    from paper_1810_11482_b300 import hxc
+    tmp = tempfile.mkdtemp(prefix="hxc_mandel_")
+    F = np.float32
+    try:
+        imgs = []
+        for q, n in enumerate(sides):
+            buf, host = dev.buffer(n * n * 3), hxc.host_empty(n * n * 3, np.uint8)
+            args = hxc.mandelbrot_args(buf, n, n, F(-2.0), F(-1.5), F(3.0 / n), F(3.0 / n), max_iter)
+            imgs.append((buf, host, args, os.path.join(tmp, "m%d.png" % q)))
+        res = {"sides": list(sides), "max_iter": max_iter, "zlib_level": level,
+               "image_bytes": [3 * n * n for n in sides]}
+        for mode in ("sync", "async"):
+            times = []
+            for rep in range(3):
+                t0 = time.perf_counter()
+                futs = [hxc.mandelbrot_png(dev, a, h, pth, level, mode == "async", slot=q)
+                        for q, (b, h, a, pth) in enumerate(imgs)]
+                assert hxc.wait_all(futs) == hxc.HXC_OK
+                times.append((time.perf_counter() - t0) * 1e3)
+            res[mode + "_ms"] = float(np.median(times[1:]))
+        res["async_speedup"] = res["sync_ms"] / res["async_ms"]
+        # the kernel alone on the largest image
+        n = sides[-1]
+        buf, cnt = imgs[-1][0], dev.buffer(n * n * 4)
+        a = hxc.mandelbrot_args(buf, n, n, F(-2.0), F(-1.5), F(3.0 / n), F(3.0 / n), max_iter, cnt)
+        dev.launch(hxc.HXC_K_MANDELBROT, a).get()
+        counts = np.empty(n * n, dtype=np.int32)
+        cnt.read_sync(counts)
+        a = hxc.mandelbrot_args(buf, n, n, F(-2.0), F(-1.5), F(3.0 / n), F(3.0 / n), max_iter)
+        kms = []
+        for _ in range(5):
+            start = timer.start()
+            kms.append(timer.stop(dev.launch(hxc.HXC_K_MANDELBROT, a, deps=[start])))
+        kms = float(np.median(kms[1:]))
+        # 7 FP32 operations per full iteration, 3 for the final escape test
+        ops = 7.0 * counts.astype(np.float64).sum() + 3.0 * float((counts < max_iter).sum())
+        peak = 148 * FP32_LANES_PER_SM * 2032e6 / 1e9
+        res["kernel"] = {"side": n, "ms": kms, "iterations": float(counts.astype(np.float64).sum()),
+                         "roofline": {"bound": "alu", "achieved": ops / (kms / 1e3) / 1e9,
+                                      "peak": peak, "unit": "Gop/s (FP32)",
+                                      "frac": ops / (kms / 1e3) / 1e9 / peak}}
+        return res
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
+def partition_bench(dev, timer, ms_exp=range(1, 9), parts=4):
+    """Sec. 5.1.2 (Algorithm 1): host-clock time of the three loops (copy in,
+    kernel, copy out, per partition) until the results are on the host, on
+    the futures layer and as plain CUDA calls on the same streams, for
+    n = 2^m * 1024 * 256 * 4; plus the device time of the kernels alone on
+    resident data."""
+    import time
+    from paper_1810_11482_b300 import hxc, synth
+    sizes = synth.partition_sizes(ms_exp, 256, parts)
+    nmax = max(sizes)
+    x_all, r_all = hxc.host_empty(nmax), hxc.host_empty(nmax)
+    synth.partition_input(nmax, out=x_all)
+    work = dev.buffer(nmax * 8)
+    rows = []
+    for m, n in zip(ms_exp, sizes):
+        x, r = x_all[:n], r_all[:n]
+        reps = max(3, min(20, (1 << 27) // n))
+        res = {"m": m, "n": n}
+        outs = {}
+        for path in ("futures", "native"):
+            def once():
+                if path == "futures":
+                    hxc.partition_run(dev, x, r, parts, work).get()
+                else:
+                    hxc.partition_run_native(dev, x, r, parts, work)
+            once()
+            best = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                once()
+                best.append((time.perf_counter() - t0) * 1e3)
+            res[path + "_ms"] = float(np.median(best))
+            outs[path] = r[:: max(1, n // 65536)].copy()
+        res["futures_over_native"] = res["futures_ms"] / res["native_ms"]
+        res["bitwise_equal_paths"] = bool(np.array_equal(outs["futures"], outs["native"]))
+        res["max_abs_err_vs_1"] = float(np.max(np.abs(r - 1.0)))
+        res["host_link_gbs"] = 16.0 * n / (res["futures_ms"] / 1e3) / 1e9  # 8 B in + 8 B out
+        # the kernels alone, data resident (a fresh copy of x before each timing)
+        kms = []
+        bounds = [i * n // parts for i in range(parts + 1)]
+        for _ in range(3):
+            work.write(x).get()
+            start = timer.start()
+            fs = [dev.launch(hxc.HXC_K_PARTITION,
+                             hxc.hxc_partition_args(work.h, bounds[i + 1] - bounds[i], bounds[i]),
+                             slot=i, deps=[start]) for i in range(parts)]
+            kms.append(timer.stop(hxc.when_all(fs)))
+        res["kernels_only_ms"] = float(np.median(kms))
+        rows.append(res)
+    return rows
 
 
 def cpu_baseline(sample_steps=3):

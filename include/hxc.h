@@ -225,7 +225,9 @@ typedef enum {
     HXC_K_ADJOINT2D = 8,
     /* Sec. 5.1.2 partition kernel k, in place on x[offset, offset+n):
      * x_i <- sqrt(sin(x_i)^2 + cos(x_i)^2), 1 up to rounding. */
-    HXC_K_PARTITION = 9
+    HXC_K_PARTITION = 9,
+    /* Sec. 5.1.3 Mandelbrot image (escape time, binary32). */
+    HXC_K_MANDELBROT = 10
 } hxc_kernel_id;
 
 typedef struct { hxc_buffer input, result; int64_t n; } hxc_sum_args;
@@ -264,6 +266,21 @@ typedef struct {
     double c;
 } hxc_adjoint2d_args;
 typedef struct { hxc_buffer x; int64_t n, offset; } hxc_partition_args;
+/* Sec. 5.1.3.  Pixel (i, j), 0 <= i < width, 0 <= j < height, is the point
+ * c = (x0 + i*dx) + (y0 + j*dy) i (each product and sum rounded to float).
+ * Its escape count k is the first k < max_iter with |z_k|^2 > 4, where
+ * z_0 = 0 and z_{k+1} = z_k^2 + c, else max_iter (a member).  One iteration
+ * in binary32: xx = x*x, yy = y*y, test xx + yy > 4, Im z' = fma(x + x, y,
+ * Im c), Re z' = (xx - yy) + Re c.  rgb: width*height*3 bytes, row-major
+ * RGB8; members black, else (9k, 5k, 13k) mod 256.  counts (may be NULL):
+ * width*height int32.  width, height <= 2^24; max_iter >= 1; a launch
+ * configuration, if given, has at most 256 threads per block. */
+typedef struct {
+    hxc_buffer rgb, counts;
+    int64_t width, height;
+    float x0, y0, dx, dy;
+    int32_t max_iter, reserved;
+} hxc_mandelbrot_args;
 
 /* Launches kernel `id` with the argument struct `args` (of size args_size,
  * which must equal the struct's size) on stream slot `slot` after deps. */
@@ -292,6 +309,29 @@ hxc_status hxc_partition_run(hxc_device dev, const double *host_x, double *host_
  * Returns when the results are on the host. */
 hxc_status hxc_partition_run_native(hxc_device dev, const double *host_x, double *host_r,
                                     int64_t n, int parts, hxc_buffer work);
+
+/* ------------------------------------------- Mandelbrot images (Sec. 5.1.3) */
+
+/* Writes an RGB8 image (height rows of width*3 bytes) as a PNG file: 8-bit
+ * truecolour, no interlace, filter type 0 on every row, zlib level `level`
+ * (-1 = zlib's default, 0..9).  Synchronous; HXC_E_INVALID on a bad
+ * argument or an I/O error (hxc_last_error names the file). */
+hxc_status hxc_png_write(const uint8_t *rgb, int64_t width, int64_t height, int level,
+                         const char *path);
+
+/* Sec. 5.1.3: one Mandelbrot image (HXC_K_MANDELBROT with *args, after
+ * deps, on stream slot `slot`), read into host_rgb (width*height*3 bytes,
+ * page-locked for an asynchronous copy), then written to `path` as by
+ * hxc_png_write.  With async_write != 0 the call returns after issuing the
+ * kernel and the copy; the file is written by a continuation on the worker
+ * pool and *out completes when the file is closed, so the caller may issue
+ * the next image (in other buffers) meanwhile -- the paper's asynchronous
+ * write.  host_rgb must stay valid and unchanged until then.  With
+ * async_write = 0 the call waits for the image, writes the file and returns
+ * with *out ready (the paper's synchronous write). */
+hxc_status hxc_mandelbrot_png(hxc_device dev, const hxc_mandelbrot_args *args, uint8_t *host_rgb,
+                              const char *path, int level, int async_write, int slot,
+                              const hxc_future *deps, int ndeps, hxc_future *out);
 
 /* ---------------------------------------------------- run-time programs */
 

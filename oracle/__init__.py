@@ -50,6 +50,13 @@ def lib():
         L.ora_varcoef2d_adjoint.restype = ctypes.c_double
         L.ora_varcoef2d_batch.argtypes = [_dp, _dp, _dp, ctypes.POINTER(_i64),
                                           ctypes.POINTER(_i64), _dp, _i64, ctypes.c_int]
+        _fp = ctypes.POINTER(ctypes.c_float)
+        L.ora_mandelbrot_counts.argtypes = [_fp, _fp, ctypes.POINTER(ctypes.c_int32), _i64,
+                                            ctypes.c_int32]
+        L.ora_mandelbrot_image.argtypes = [ctypes.POINTER(ctypes.c_uint8),
+                                           ctypes.POINTER(ctypes.c_int32), _i64, _i64,
+                                           ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_float, ctypes.c_int32]
         _lib = L
     return _lib
 
@@ -82,6 +89,29 @@ def partition_k(x):
     elementwise, with the C library's sin, cos and sqrt."""
     x = _f64(x)
     return np.sqrt(np.sin(x) ** 2 + np.cos(x) ** 2)
+
+
+def mandelbrot_counts(cr, ci, max_iter):
+    """Sec. 5.1.3: escape counts of the points c = cr + i ci (binary32) under
+    z <- z^2 + c from z = 0 (max_iter for points that do not escape)."""
+    cr = np.ascontiguousarray(cr, dtype=np.float32)
+    ci = np.ascontiguousarray(ci, dtype=np.float32)
+    cnt = np.empty(cr.size, dtype=np.int32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib().ora_mandelbrot_counts(cr.ctypes.data_as(fp), ci.ctypes.data_as(fp),
+                                cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cr.size, max_iter)
+    return cnt
+
+
+def mandelbrot_image(width, height, x0, y0, dx, dy, max_iter):
+    """Sec. 5.1.3: the RGB8 image (height, width, 3) and escape counts
+    (height, width) of pixel c = (x0 + i dx) + (y0 + j dy) i."""
+    rgb = np.empty((height, width, 3), dtype=np.uint8)
+    cnt = np.empty((height, width), dtype=np.int32)
+    lib().ora_mandelbrot_image(rgb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                               cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), width, height,
+                               x0, y0, dx, dy, max_iter)
+    return rgb, cnt
 
 
 def heat1d(u0, r, steps):

@@ -26,8 +26,12 @@
  *  - Partitioning (Algorithm 1) does not change the mathematics: the oracle
  *    works on whole domains.
  *
+ *  - Mandelbrot (Sec. 5.1.3): escape-time iteration in binary32 with a
+ *    fixed rounding sequence (see the routine); the only non-FP64 routine.
+ *
  * Parity status: every routine here is pinned by the CPU test-suite against
- * closed forms, exact rational brute force or dense-matrix constructions.
+ * closed forms, exact rational brute force, dense-matrix constructions or
+ * (Mandelbrot) exactly known orbits and the set's area.
  */
 #include <math.h>
 #include <stdint.h>
@@ -292,4 +296,57 @@ void ora_varcoef2d_batch(const double *u0, const double *kap, double *out,
     for (i64 p = 0; p < nprob; p++)
         ora_varcoef2d(u0 + offset[p], kap + offset[p], out + offset[p],
                       side[p], side[p], c[p], steps);
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. 5.1.3 Mandelbrot set, escape-time form, in binary32 (the paper does
+ * not fix the precision; this reading takes single precision and this
+ * exact rounding sequence, which the device kernel follows too).
+ *   z_0 = 0;  for k = 0, 1, ..., max_iter-1:
+ *       if |z_k|^2 > 4 the count is k;  z_{k+1} = z_k^2 + c.
+ *   The count is max_iter if no z_k escapes (c taken as a member).
+ * One iteration, with x = Re z, y = Im z, each operation rounded to float:
+ *   xx = x*x, yy = y*y, escape test xx + yy > 4,
+ *   Im z' = fma(x + x, y, Im c)   (2xy + Im c, one rounding; x + x is exact),
+ *   Re z' = (xx - yy) + Re c.
+ * Pixel (i, j) of a width x height image is c = (x0 + i*dx) + (y0 + j*dy) i,
+ * each product and sum rounded to float.
+ * Colour: members black; otherwise (R, G, B) = (9k, 5k, 13k) mod 256.
+ * ---------------------------------------------------------------------- */
+static int32_t mandel_count(float cr, float ci, int32_t max_iter) {
+    float x = 0.0f, y = 0.0f;
+    for (int32_t k = 0; k < max_iter; k++) {
+        float xx = x * x, yy = y * y;
+        if (xx + yy > 4.0f) return k;
+        float ny = fmaf(x + x, y, ci);
+        x = (xx - yy) + cr;
+        y = ny;
+    }
+    return max_iter;
+}
+
+void ora_mandelbrot_counts(const float *cr, const float *ci, int32_t *cnt, i64 n,
+                           int32_t max_iter) {
+    for (i64 p = 0; p < n; p++) cnt[p] = mandel_count(cr[p], ci[p], max_iter);
+}
+
+void ora_mandelbrot_image(uint8_t *rgb, int32_t *cnt, i64 width, i64 height, float x0,
+                          float y0, float dx, float dy, int32_t max_iter) {
+    for (i64 j = 0; j < height; j++) {
+        float ci = y0 + (float)j * dy;
+        for (i64 i = 0; i < width; i++) {
+            float cr = x0 + (float)i * dx;
+            int32_t k = mandel_count(cr, ci, max_iter);
+            i64 p = j * width + i;
+            if (cnt) cnt[p] = k;
+            uint8_t *o = rgb + 3 * p;
+            if (k == max_iter) {
+                o[0] = o[1] = o[2] = 0;
+            } else {
+                o[0] = (uint8_t)((9 * (uint32_t)k) & 255u);
+                o[1] = (uint8_t)((5 * (uint32_t)k) & 255u);
+                o[2] = (uint8_t)((13 * (uint32_t)k) & 255u);
+            }
+        }
+    }
 }

@@ -70,7 +70,7 @@ def build(force=False, verbose=False):
     changed = any(c for _, c in results) or not os.path.exists(LIB)
     if changed or force:
         tmp = LIB + ".tmp"
-        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared", "-lpthread"]
+        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared", "-lpthread", "-lz"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -652,6 +652,25 @@ hxc_status hxc_launch(hxc_device dh, hxc_kernel_id id, const void *args, size_t 
             op = [=](cudaStream_t s) { return k::prk(ip, optr, n, pc ? &cfg : nullptr, s); };
             break;
         }
+        case HXC_K_MANDELBROT: {
+            ARGS(hxc_mandelbrot_args);
+            if (a.width < 0 || a.height < 0 || a.max_iter < 1 || !cfg_ok(pc, 32, 256)) goto bad;
+            if (a.width > ((int64_t)1 << 24) || a.height > ((int64_t)1 << 24)) goto bad;
+            const size_t npx = (size_t)a.width * (size_t)a.height;
+            BUF(img, a.rgb, npx * 3, "mandelbrot.rgb");
+            uint8_t *rp = (uint8_t *)img->ptr;
+            int32_t *cp = nullptr;
+            if (a.counts) {
+                BUF(cb, a.counts, npx * 4, "mandelbrot.counts");
+                cp = (int32_t *)cb->ptr;
+            }
+            const hxc_mandelbrot_args m = a;
+            op = [=](cudaStream_t s) {
+                return k::mandelbrot(rp, cp, m.width, m.height, m.x0, m.y0, m.dx, m.dy, m.max_iter,
+                                     pc ? &cfg : nullptr, s);
+            };
+            break;
+        }
         case HXC_K_PARTITION: {
             ARGS(hxc_partition_args);
             if (a.n < 0 || a.offset < 0 || !cfg_ok(pc, 32, 1024)) goto bad;

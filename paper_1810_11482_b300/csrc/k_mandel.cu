@@ -1,0 +1,75 @@
+// Sec. 5.1.3 Mandelbrot kernel: escape-time iteration of z <- z^2 + c from
+// z = 0, one pixel per thread, in binary32 with an explicit rounding
+// sequence (round-to-nearest intrinsics, so the compiler fuses nothing
+// else):  xx = x*x, yy = y*y, escape when xx + yy > 4,
+// Im z' = fma(x + x, y, Im c), Re z' = (xx - yy) + Re c.
+// Pixel (i, j) is c = (x0 + i*dx) + (y0 + j*dy) i, each step rounded.
+//
+// The work per pixel ranges from one iteration to max_iter, so a warp owns
+// an 8 x 4 pixel tile (neighbouring pixels tend to escape together, which
+// keeps the warp's lanes busy) and warps stride over the tiles of the image
+// in an interleaved order, spreading the expensive interior over all SMs.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace hxc {
+namespace k {
+
+namespace {
+
+constexpr int kTileW = 8, kTileH = 4;
+
+__global__ void __launch_bounds__(256) k_mandelbrot(uint8_t *__restrict__ rgb,
+                                                     int32_t *__restrict__ counts, int64_t width,
+                                                     int64_t height, float x0, float y0, float dx,
+                                                     float dy, int32_t max_iter) {
+    const int lane = threadIdx.x & 31;
+    const int64_t tiles_x = (width + kTileW - 1) / kTileW;
+    const int64_t tiles = tiles_x * ((height + kTileH - 1) / kTileH);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles;
+         t += warps) {
+        const int64_t i = (t % tiles_x) * kTileW + (lane % kTileW);
+        const int64_t j = (t / tiles_x) * kTileH + (lane / kTileW);
+        if (i >= width || j >= height) continue;
+        const float cr = __fadd_rn(x0, __fmul_rn((float)i, dx));
+        const float ci = __fadd_rn(y0, __fmul_rn((float)j, dy));
+        float x = 0.0f, y = 0.0f;
+        int32_t k = 0;
+        for (; k < max_iter; k++) {
+            const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y);
+            if (__fadd_rn(xx, yy) > 4.0f) break;
+            y = __fmaf_rn(__fadd_rn(x, x), y, ci);
+            x = __fadd_rn(__fsub_rn(xx, yy), cr);
+        }
+        const int64_t p = j * width + i;
+        if (counts) counts[p] = k;
+        const uint32_t u = (uint32_t)k;
+        const bool member = k == max_iter;
+        rgb[3 * p + 0] = member ? 0 : (uint8_t)(u * 9u);
+        rgb[3 * p + 1] = member ? 0 : (uint8_t)(u * 5u);
+        rgb[3 * p + 2] = member ? 0 : (uint8_t)(u * 13u);
+    }
+}
+
+}  // namespace
+
+cudaError_t mandelbrot(uint8_t *rgb, int32_t *counts, int64_t width, int64_t height, float x0,
+                       float y0, float dx, float dy, int32_t max_iter, const hxc_launch_cfg *cfg,
+                       cudaStream_t s) {
+    if (width == 0 || height == 0) return cudaSuccess;
+    const int64_t tiles = ((width + kTileW - 1) / kTileW) * ((height + kTileH - 1) / kTileH);
+    unsigned b = 256, g;
+    if (cfg) {
+        b = cfg->block[0] * cfg->block[1] * cfg->block[2];
+        g = cfg->grid[0] * cfg->grid[1] * cfg->grid[2];
+    } else {
+        g = (unsigned)std::min<int64_t>((tiles + 7) / 8, (int64_t)sm_count() * 8);
+    }
+    k_mandelbrot<<<g, b, 0, s>>>(rgb, counts, width, height, x0, y0, dx, dy, max_iter);
+    return cudaGetLastError();
+}
+
+}  // namespace k
+}  // namespace hxc

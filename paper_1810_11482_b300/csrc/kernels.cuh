@@ -25,6 +25,11 @@ cudaError_t sum_u32(const uint32_t *in, unsigned long long *result, int64_t n,
 cudaError_t prk(const double *in, double *out, int64_t n, const hxc_launch_cfg *cfg,
                 cudaStream_t s);
 cudaError_t partition(double *x, int64_t n, const hxc_launch_cfg *cfg, cudaStream_t s);
+// Sec. 5.1.3: RGB8 image (and optional int32 escape counts) of the
+// Mandelbrot set; pixel (i, j) is c = (x0 + i dx) + (y0 + j dy) i.
+cudaError_t mandelbrot(uint8_t *rgb, int32_t *counts, int64_t width, int64_t height, float x0,
+                       float y0, float dx, float dy, int32_t max_iter, const hxc_launch_cfg *cfg,
+                       cudaStream_t s);
 
 // dst[lo, lo+count) <- `steps` periodic FTCS steps of src (period n).
 cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,

@@ -37,6 +37,7 @@ HXC_K_HEAT3D = 6
 HXC_K_VARCOEF2D = 7
 HXC_K_ADJOINT2D = 8
 HXC_K_PARTITION = 9
+HXC_K_MANDELBROT = 10
 
 HXC_MODE_PLAIN = 0
 HXC_MODE_GRAPH = 1
@@ -51,7 +52,8 @@ c_st = ctypes.c_int
 i64 = ctypes.c_int64
 HOST_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
 # argument structs beyond the core set, checked against the header by the tests
-EXTRA_STRUCTS = ["hxc_heat3d_args", "hxc_varcoef2d_args", "hxc_adjoint2d_args", "hxc_kernel_arg"]
+EXTRA_STRUCTS = ["hxc_heat3d_args", "hxc_varcoef2d_args", "hxc_adjoint2d_args", "hxc_kernel_arg",
+                 "hxc_mandelbrot_args"]
 
 
 class hxc_launch_cfg(ctypes.Structure):
@@ -98,6 +100,12 @@ class hxc_adjoint2d_args(ctypes.Structure):
 
 class hxc_partition_args(ctypes.Structure):
     _fields_ = [("x", c_buf), ("n", i64), ("offset", i64)]
+
+
+class hxc_mandelbrot_args(ctypes.Structure):
+    _fields_ = [("rgb", c_buf), ("counts", c_buf), ("width", i64), ("height", i64),
+                ("x0", ctypes.c_float), ("y0", ctypes.c_float), ("dx", ctypes.c_float),
+                ("dy", ctypes.c_float), ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class hxc_kernel_arg(ctypes.Structure):
@@ -208,6 +216,10 @@ _SIGS = {
                                  ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut)]),
     "hxc_partition_run_native": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, ctypes.c_int,
                                         c_buf]),
+    "hxc_png_write": (c_st, [ctypes.c_void_p, i64, i64, ctypes.c_int, ctypes.c_char_p]),
+    "hxc_mandelbrot_png": (c_st, [c_dev, ctypes.POINTER(hxc_mandelbrot_args), ctypes.c_void_p,
+                                  ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut)]),
     "hxc_program_create_with_source": (c_st, [c_dev, ctypes.c_char_p, ctypes.c_char_p,
                                               ctypes.POINTER(ctypes.c_void_p)]),
     "hxc_program_create_with_file": (c_st, [c_dev, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -600,6 +612,35 @@ def partition_run_native(dev, host_x, host_r, parts, work):
     check(lib().hxc_partition_run_native(dev.h, _f64_host(host_x, "host_x"),
                                          _f64_host(host_r, "host_r"), host_x.size, parts, work.h),
           "partition_run_native")
+
+
+def mandelbrot_args(rgb, width, height, x0, y0, dx, dy, max_iter, counts=None):
+    return hxc_mandelbrot_args(rgb.h, counts.h if counts is not None else None, width, height,
+                               x0, y0, dx, dy, max_iter, 0)
+
+
+def png_write(rgb, path, level=-1):
+    """rgb: uint8 array (height, width, 3), C-contiguous."""
+    if not (isinstance(rgb, np.ndarray) and rgb.dtype == np.uint8 and rgb.ndim == 3
+            and rgb.shape[2] == 3 and rgb.flags.c_contiguous):
+        raise ValueError("rgb must be a C-contiguous uint8 array of shape (h, w, 3)")
+    check(lib().hxc_png_write(rgb.ctypes.data, rgb.shape[1], rgb.shape[0], level,
+                              str(path).encode()), "png_write")
+
+
+def mandelbrot_png(dev, args, host_rgb, path, level=-1, async_write=True, slot=0, deps=()):
+    """One image to a PNG file (hxc_mandelbrot_png); returns the future of
+    the file write.  host_rgb: uint8 array of width*height*3 bytes."""
+    if host_rgb.dtype != np.uint8 or host_rgb.size < args.width * args.height * 3:
+        raise ValueError("host_rgb must be a uint8 array of width*height*3 bytes")
+    arr, n = _futs(deps)
+    out = c_fut()
+    check(lib().hxc_mandelbrot_png(dev.h, ctypes.byref(args), host_rgb.ctypes.data,
+                                   str(path).encode(), level, int(bool(async_write)), slot, arr, n,
+                                   ctypes.byref(out)), "mandelbrot_png")
+    f = Future(out.value)
+    f._host = host_rgb
+    return f
 
 
 class Program:

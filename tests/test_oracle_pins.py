@@ -461,3 +461,67 @@ def test_partition_kernel_is_one_and_sizes():
     assert np.max(np.abs(np.sqrt(np.abs(np.sin(x) ** 2 - np.cos(x) ** 2)) - 1.0)) > 0.5
     assert synth.partition_sizes() == [1 << e for e in range(21, 29)]
     assert np.array_equal(synth.partition_input(5), [0.0, 1.0, 2.0, 3.0, 4.0])
+
+
+def test_mandelbrot_exact_orbits():
+    """Sec. 5.1.3, points with orbits exact in binary32: 0, -1, -2, i, 1/4 and
+    -3/4 stay bounded (members); c = 1 runs 0, 1, 2, 5 and escapes at k = 3;
+    c = 2i runs 0, 2i, -4 + 2i and escapes at k = 2 (|2i|^2 = 4 is not > 4);
+    c = 3 and c = 5/2 escape at k = 1 (z_0 = 0 is inside, z_1 = c is not)."""
+    cr = [0.0, -1.0, -2.0, 0.0, 0.25, -0.75, 1.0, 0.0, 3.0, 2.5]
+    ci = [0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 2.0, 0.0, 0.0]
+    got = oracle.mandelbrot_counts(cr, ci, 300)
+    assert got.tolist() == [300, 300, 300, 300, 300, 300, 3, 2, 1, 1]
+
+
+def _exact_count(cr, ci, max_iter):
+    """Escape count in exact rational arithmetic; also the smallest distance
+    of |z_k|^2 from 4 seen before the decision."""
+    c = (Fraction(float(cr)), Fraction(float(ci)))
+    x = y = Fraction(0)
+    margin = Fraction(10)
+    for k in range(max_iter):
+        m = x * x + y * y
+        margin = min(margin, abs(m - 4))
+        if m > 4:
+            return k, margin
+        x, y = x * x - y * y + c[0], 2 * x * y + c[1]
+    return max_iter, margin
+
+
+def test_mandelbrot_against_exact_arithmetic_and_symmetry():
+    """Brute force: short orbits in exact rational arithmetic decide the same
+    count as the binary32 oracle wherever |z_k|^2 stays clear of 4 (the
+    rounding of a few float steps cannot cross the threshold there); and
+    conjugate points escape together (every step is odd in Im z)."""
+    cr = synth.uniform(21, 3000, lo=-2.5, hi=1.5).astype(np.float32)
+    ci = synth.uniform(22, 3000, lo=-1.6, hi=1.6).astype(np.float32)
+    max_iter = 6
+    got = oracle.mandelbrot_counts(cr, ci, max_iter)
+    checked = 0
+    for a, b, g in zip(cr, ci, got):
+        want, margin = _exact_count(a, b, max_iter)
+        if margin > Fraction(1, 20):
+            assert g == want, (a, b, g, want)
+            checked += 1
+    assert checked > 2000
+    assert np.array_equal(oracle.mandelbrot_counts(cr, -ci, 200), oracle.mandelbrot_counts(cr, ci, 200))
+
+
+def test_mandelbrot_area_and_image():
+    """The members of an 800 x 800 grid over [-2, 1] x [-1.5, 1.5] (500
+    iterations) cover about the set's area, 1.5066; the image colours follow
+    the counts (members black, else (9k, 5k, 13k) mod 256)."""
+    n, it = 800, 500
+    h = np.float32(3.0 / n)
+    rgb, cnt = oracle.mandelbrot_image(n, n, np.float32(-2.0), np.float32(-1.5), h, h, it)
+    area = (cnt == it).mean() * 9.0
+    assert abs(area - 1.5066) < 0.02
+    k = cnt.astype(np.uint32)
+    want = np.stack([(9 * k) & 255, (5 * k) & 255, (13 * k) & 255], axis=-1).astype(np.uint8)
+    want[cnt == it] = 0
+    assert np.array_equal(rgb, want)
+    # pixel (i, j) is the point (x0 + i dx, y0 + j dy)
+    j, i = 123, 456
+    assert cnt[j, i] == oracle.mandelbrot_counts([np.float32(-2.0) + np.float32(i) * h],
+                                                 [np.float32(-1.5) + np.float32(j) * h], it)[0]
