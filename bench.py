@@ -409,44 +409,65 @@ def secondary(dev, timer, peaks):
 FP32_LANES_PER_SM = 128  # FP32 operations per SM per clock (an FMA counts as one)
 
 
-def mandelbrot_bench(dev, timer, sides=(1024, 2048, 4096, 8192), max_iter=256, level=1):
-    """Sec. 5.1.3: images of increasing size, each computed on the device,
-    copied back and written as a PNG file (zlib level 1); the whole sequence
-    timed on the host clock with the files written synchronously after each
-    image, and as continuations that overlap the next images.  Plus the
-    kernel alone on the largest image against the FP32 issue rate."""
+def mandelbrot_frames(n, frames, max_iter):
+    """Argument sets of a zoom sequence of `frames` n x n images towards the
+    point -0.7436 + 0.1318i, the view halving in width from frame to frame
+    (from [-2, 1] x [-1.5, 1.5])."""
+    F = np.float32
+    out = []
+    cx, cy = -0.7436439, 0.1318259
+    for f in range(frames):
+        w = 3.0 * 0.5 ** f
+        x0 = -2.0 + (cx + 2.0) * (1 - 0.5 ** f)
+        y0 = -1.5 + (cy + 1.5) * (1 - 0.5 ** f)
+        out.append((F(x0), F(y0), F(w / n), F(w / n), max_iter))
+    return out
+
+
+def mandelbrot_bench(dev, timer, sides=(1024, 2048, 4096, 8192), frames=8, max_iter=256, level=1):
+    """Sec. 5.1.3: for each image size, a sequence of `frames` images (a zoom)
+    computed on the device, copied back and written as PNG files (zlib
+    level 1); host-clock time of the sequence with each file written
+    synchronously before the next image is issued, and with the writes as
+    continuations that overlap the next images and one another.  Plus the
+    kernel alone on the first frame of the largest size against the FP32
+    issue rate."""
     import shutil
     import tempfile
     import time
     from paper_1810_11482_b300 import hxc
     tmp = tempfile.mkdtemp(prefix="hxc_mandel_")
-    F = np.float32
     try:
-        imgs = []
-        for q, n in enumerate(sides):
-            buf, host = dev.buffer(n * n * 3), hxc.host_empty(n * n * 3, np.uint8)
-            args = hxc.mandelbrot_args(buf, n, n, F(-2.0), F(-1.5), F(3.0 / n), F(3.0 / n), max_iter)
-            imgs.append((buf, host, args, os.path.join(tmp, "m%d.png" % q)))
-        res = {"sides": list(sides), "max_iter": max_iter, "zlib_level": level,
-               "image_bytes": [3 * n * n for n in sides]}
-        for mode in ("sync", "async"):
-            times = []
-            for rep in range(3):
-                t0 = time.perf_counter()
-                futs = [hxc.mandelbrot_png(dev, a, h, pth, level, mode == "async", slot=q)
-                        for q, (b, h, a, pth) in enumerate(imgs)]
-                assert hxc.wait_all(futs) == hxc.HXC_OK
-                times.append((time.perf_counter() - t0) * 1e3)
-            res[mode + "_ms"] = float(np.median(times[1:]))
-        res["async_speedup"] = res["sync_ms"] / res["async_ms"]
-        # the kernel alone on the largest image
-        n = sides[-1]
-        buf, cnt = imgs[-1][0], dev.buffer(n * n * 4)
-        a = hxc.mandelbrot_args(buf, n, n, F(-2.0), F(-1.5), F(3.0 / n), F(3.0 / n), max_iter, cnt)
-        dev.launch(hxc.HXC_K_MANDELBROT, a).get()
+        nmax = max(sides)
+        bufs = [dev.buffer(nmax * nmax * 3) for _ in range(frames)]
+        hosts = [hxc.host_empty(nmax * nmax * 3, np.uint8) for _ in range(frames)]
+        res = {"frames": frames, "max_iter": max_iter, "zlib_level": level, "sizes": []}
+        for n in sides:
+            args = [hxc.mandelbrot_args(bufs[f], n, n, *fr) for f, fr in enumerate(mandelbrot_frames(n, frames, max_iter))]
+            row = {"side": n, "image_bytes": 3 * n * n}
+            for mode in ("sync", "async"):
+                times = []
+                for rep in range(3):
+                    names = [os.path.join(tmp, "%s%d_%d_%d.png" % (mode, n, rep, f)) for f in range(frames)]
+                    t0 = time.perf_counter()
+                    futs = [hxc.mandelbrot_png(dev, a, hosts[f], names[f], level, mode == "async",
+                                               slot=f % 4)
+                            for f, a in enumerate(args)]
+                    assert hxc.wait_all(futs) == hxc.HXC_OK
+                    times.append((time.perf_counter() - t0) * 1e3)
+                    for nm in names:  # new files every time: no truncation inside the timing
+                        os.remove(nm)
+                row[mode + "_ms"] = float(np.median(times[1:]))
+            row["async_speedup"] = row["sync_ms"] / row["async_ms"]
+            res["sizes"].append(row)
+        # the kernel alone on the first frame of the largest size
+        n = nmax
+        cnt = dev.buffer(n * n * 4)
+        fr = mandelbrot_frames(n, 1, max_iter)[0]
+        dev.launch(hxc.HXC_K_MANDELBROT, hxc.mandelbrot_args(bufs[0], n, n, *fr, counts=cnt)).get()
         counts = np.empty(n * n, dtype=np.int32)
         cnt.read_sync(counts)
-        a = hxc.mandelbrot_args(buf, n, n, F(-2.0), F(-1.5), F(3.0 / n), F(3.0 / n), max_iter)
+        a = hxc.mandelbrot_args(bufs[0], n, n, *fr)
         kms = []
         for _ in range(5):
             start = timer.start()
