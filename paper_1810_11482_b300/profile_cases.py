@@ -4,6 +4,8 @@
     python -m paper_1810_11482_b300.profile_cases heat3d [nz ny nx] [steps]
     python -m paper_1810_11482_b300.profile_cases batch [nprob] [steps]
     python -m paper_1810_11482_b300.profile_cases adjoint [n] [steps]
+    python -m paper_1810_11482_b300.profile_cases partition [n] [parts]
+    python -m paper_1810_11482_b300.profile_cases mandelbrot [side] [max_iter]
 
 Each case uploads seeded synthetic inputs, runs the path once through the C
 ABI and exits 0; sizes default to fields larger than the 126 MB L2 but small
@@ -61,7 +63,26 @@ def adjoint(n=2048, steps=20):
     return st.kernel_launches
 
 
-CASES = {"heat2d": heat2d, "heat3d": heat3d, "batch": batch, "adjoint": adjoint}
+def partition(n=1 << 24, parts=4):
+    dev = hxc.get_all_devices(2, 0)[0]
+    x, r = hxc.host_empty(n), hxc.host_empty(n)
+    synth.partition_input(n, out=x)
+    hxc.partition_run(dev, x, r, parts, dev.buffer(n * 8)).get()
+    return parts
+
+
+def mandelbrot(side=4096, max_iter=256):
+    dev = hxc.get_all_devices(2, 0)[0]
+    f32 = np.float32
+    rgb = dev.buffer(side * side * 3)
+    a = hxc.mandelbrot_args(rgb, side, side, f32(-2.0), f32(-1.5), f32(3.0 / side), f32(3.0 / side),
+                            max_iter)
+    dev.launch(hxc.HXC_K_MANDELBROT, a).get()
+    return 1
+
+
+CASES = {"heat2d": heat2d, "heat3d": heat3d, "batch": batch, "adjoint": adjoint,
+         "partition": partition, "mandelbrot": mandelbrot}
 
 if __name__ == "__main__":
     name = sys.argv[1]
