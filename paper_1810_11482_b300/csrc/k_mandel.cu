@@ -20,6 +20,43 @@ namespace {
 
 constexpr int kTileW = 8, kTileH = 4;
 
+// One iteration from (x, y): the escape test of z_k and z_{k+1}.
+struct Iter {
+    float x, y;
+    bool escaped;
+};
+__device__ __forceinline__ Iter step(float x, float y, float cr, float ci) {
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y);
+    return {__fadd_rn(__fsub_rn(xx, yy), cr), __fmaf_rn(__fadd_rn(x, x), y, ci),
+            __fadd_rn(xx, yy) > 4.0f};
+}
+
+// The escape count.  Iterations run in groups of four with the four escape
+// tests joined into one branch; on an escape the first test that fired, in
+// order, gives the count, so the result is that of testing after every
+// iteration (values past the escape may overflow; they are never used).
+__device__ __forceinline__ int32_t escape_count(float cr, float ci, int32_t max_iter) {
+    float x = 0.0f, y = 0.0f;
+    int32_t k = 0;
+    for (; k + 4 <= max_iter; k += 4) {
+        const Iter a = step(x, y, cr, ci);
+        const Iter b = step(a.x, a.y, cr, ci);
+        const Iter c = step(b.x, b.y, cr, ci);
+        const Iter d = step(c.x, c.y, cr, ci);
+        if (a.escaped | b.escaped | c.escaped | d.escaped)
+            return k + (a.escaped ? 0 : b.escaped ? 1 : c.escaped ? 2 : 3);
+        x = d.x;
+        y = d.y;
+    }
+    for (; k < max_iter; k++) {
+        const Iter a = step(x, y, cr, ci);
+        if (a.escaped) return k;
+        x = a.x;
+        y = a.y;
+    }
+    return max_iter;
+}
+
 __global__ void __launch_bounds__(256) k_mandelbrot(uint8_t *__restrict__ rgb,
                                                      int32_t *__restrict__ counts, int64_t width,
                                                      int64_t height, float x0, float y0, float dx,
@@ -33,16 +70,9 @@ __global__ void __launch_bounds__(256) k_mandelbrot(uint8_t *__restrict__ rgb,
         const int64_t i = (t % tiles_x) * kTileW + (lane % kTileW);
         const int64_t j = (t / tiles_x) * kTileH + (lane / kTileW);
         if (i >= width || j >= height) continue;
-        const float cr = __fadd_rn(x0, __fmul_rn((float)i, dx));
-        const float ci = __fadd_rn(y0, __fmul_rn((float)j, dy));
-        float x = 0.0f, y = 0.0f;
-        int32_t k = 0;
-        for (; k < max_iter; k++) {
-            const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y);
-            if (__fadd_rn(xx, yy) > 4.0f) break;
-            y = __fmaf_rn(__fadd_rn(x, x), y, ci);
-            x = __fadd_rn(__fsub_rn(xx, yy), cr);
-        }
+        const float cr = __fadd_rn(x0, __fmul_rn((float)(int)i, dx));
+        const float ci = __fadd_rn(y0, __fmul_rn((float)(int)j, dy));
+        const int32_t k = escape_count(cr, ci, max_iter);
         const int64_t p = j * width + i;
         if (counts) counts[p] = k;
         const uint32_t u = (uint32_t)k;

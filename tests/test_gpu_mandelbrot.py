@@ -36,9 +36,10 @@ def device_image(dev, w, h, x0, y0, dx, dy, it, cfg=None):
 
 CASES = [
     (333, 251, F(-2.0), F(-1.5), F(3.0 / 333), F(3.0 / 251), 300),   # whole set, ragged tiles
-    (257, 129, F(-0.7485), F(0.0999), F(2e-5), F(2e-5), 1000),       # near the boundary
+    (257, 129, F(-0.7485), F(0.0999), F(2e-5), F(2e-5), 1001),       # near the boundary
     (8, 4, F(-2.0), F(-1.0), F(0.4), F(0.5), 1),                     # one tile, max_iter 1
-    (1, 1, F(0.0), F(0.0), F(1.0), F(1.0), 50),
+    (1, 1, F(0.0), F(0.0), F(1.0), F(1.0), 7),
+    (64, 48, F(-1.9), F(-1.2), F(0.05), F(0.05), 6),                  # groups of 4 + a tail of 2
 ]
 
 
