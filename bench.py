@@ -497,7 +497,7 @@ def partition_bench(dev, timer, ms_exp=range(1, 9), parts=4):
     nmax = max(sizes)
     x_all, r_all = hxc.host_empty(nmax), hxc.host_empty(nmax)
     synth.partition_input(nmax, out=x_all)
-    work = dev.buffer(nmax * 8)
+    work, side = dev.buffer(nmax * 8), dev.buffer(nmax * 8)
     rows = []
     for m, n in zip(ms_exp, sizes):
         x, r = x_all[:n], r_all[:n]
@@ -534,7 +534,23 @@ def partition_bench(dev, timer, ms_exp=range(1, 9), parts=4):
             kms.append(timer.stop(hxc.when_all(fs)))
         res["kernels_only_ms"] = float(np.median(kms))
         rows.append(res)
-    return rows
+    # the host link alone: the whole largest vector in and out at the same time
+    # (one copy each way on two stream slots), the bound of Algorithm 1
+    n = nmax
+    link = []
+    for _ in range(4):
+        t0 = time.perf_counter()
+        fw = work.write(x_all, slot=0)
+        fr = side.read(r_all, slot=1)
+        assert hxc.wait_all([fw, fr]) == hxc.HXC_OK
+        link.append((time.perf_counter() - t0) * 1e3)
+    link_gbs = 16.0 * n / (float(np.median(link[1:])) / 1e3) / 1e9
+    last = rows[-1]
+    return {"sizes": rows,
+            "roofline": {"bound": "host link", "achieved": last["host_link_gbs"], "peak": link_gbs,
+                         "unit": "GB/s", "frac": last["host_link_gbs"] / link_gbs, "n": n,
+                         "peak_source": "measured here: 8n bytes host->device and 8n bytes "
+                                        "device->host copied concurrently on two streams"}}
 
 
 def cpu_baseline(sample_steps=3):

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "runtime.hpp"
+#include "tune.hpp"
 
 namespace hxc {
 namespace drv {
@@ -52,6 +53,8 @@ inline std::string key_of(const char *what, std::initializer_list<double> vals,
                    std::initializer_list<const void *> ptrs) {
     std::string k = what;
     char buf[64];
+    snprintf(buf, sizeof buf, "|tune%llu", (unsigned long long)tune::generation());
+    k += buf;
     for (double v : vals) {
         snprintf(buf, sizeof buf, "|%.17g", v);
         k += buf;

@@ -3,6 +3,7 @@
 
 #include <dlfcn.h>
 
+#include <atomic>
 #include <cctype>
 #include <cstdio>
 #include <cstdlib>
@@ -28,6 +29,7 @@ Knob g_knobs[] = {
     {"heat2d.rows", 8, 1, 4096},      // rows per warp of the 2D kernel
     {"heat2d.occupancy", 4, 4, 6},    // compiled minimum of CTAs per SM
     {"heat3d.zchunks", 0, 0, 64},     // z chunks per launch (0: fill whole waves)
+    {"heat3d.variant", 1, 0, 1},      // 0: copied plane registers, 1: rotated
     {"heat1d.tb_ctas", 0, 0, 1 << 16},  // CTAs per partition of the 1D blocked kernel (0: SMs/parts)
     {"batch.ctas_per_sm", 4, 1, 16},  // CTAs per SM of the persistent batch kernel
 };
@@ -98,11 +100,17 @@ int64_t get(const char *key) {
 
 bool known(const char *key) { return find(key) != nullptr; }
 
+std::atomic<uint64_t> g_generation{0};
+
+uint64_t generation() { return g_generation.load(); }
+
 bool set(const char *key, int64_t value) {
     std::lock_guard<std::mutex> lk(g_m);
     Knob *k = find(key);
     if (!k) return false;
-    k->value = value < k->lo ? k->lo : (value > k->hi ? k->hi : value);
+    const int64_t v = value < k->lo ? k->lo : (value > k->hi ? k->hi : value);
+    if (v != k->value) g_generation.fetch_add(1);
+    k->value = v;
     return true;
 }
 

@@ -17,6 +17,10 @@ int64_t get(const char *key);
 // Sets a known knob (clamped to its range); false for an unknown key.
 bool set(const char *key, int64_t value);
 bool known(const char *key);
+// Incremented by every change of a knob's value (set or cache load); part
+// of the key of every cached CUDA graph, so that a graph captured before a
+// change (with other launch shapes or kernel variants) is not replayed.
+uint64_t generation();
 // Loads {"sm_<major><minor>": {"key": int, ...}, ...} for the given
 // architecture (or a flat {"key": int} object).  Returns HXC_E_INVALID on a
 // malformed file, HXC_OK when the file is absent is not an error for the
