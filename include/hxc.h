@@ -523,8 +523,9 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *                  kernel is compiled for, 4..6 (default 4).
  *   "heat3d.zchunks"  z chunks of a 3D launch, 0 = fill whole waves.
  *   "heat3d.variant"  3D kernel form: 0 = plane registers copied each z
- *                  step, 1 = plane registers rotated (z loop unrolled by 3,
- *                  default).
+ *                  step, 1 = plane registers rotated (z loop unrolled by 3),
+ *                  2 = rotated, arithmetic on paired FP32 instructions
+ *                  (default).
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
  *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).

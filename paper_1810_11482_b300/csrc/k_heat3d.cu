@@ -310,6 +310,169 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Variant 2: variant 1 with the arithmetic on packed pairs.  The two
+// x-adjacent cells of each of the thread's rows are held as one 64-bit pair
+// and updated with the paired FP32 instructions of sm_100-class GPUs
+// (add.rn.f32x2, fma.rn.f32x2), which round each half exactly as the scalar
+// instruction does: the canonical expression, evaluated on two cells per
+// instruction.
+namespace {
+
+typedef unsigned long long f2;  // two floats; the low half is the lower x
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_of(f2 v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float hi_of(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// ftcs7 on two cells at once (same operation order and rounding)
+__device__ __forceinline__ f2 ftcs7x2(f2 u, f2 xm, f2 xp, f2 ym, f2 yp, f2 zm, f2 zp, f2 r2,
+                                      f2 m6) {
+    const f2 s = add2(add2(add2(xm, xp), add2(ym, yp)), add2(zm, zp));
+    return fma2(r2, fma2(m6, u, s), u);
+}
+
+__device__ __forceinline__ void load2x2(f2 (&v)[2], const float *__restrict__ src, size_t zo,
+                                        const Cols &c) {
+    if (c.pair) {
+        v[0] = __ldg(reinterpret_cast<const unsigned long long *>(src + zo + c.o00));
+        v[1] = __ldg(reinterpret_cast<const unsigned long long *>(src + zo + c.o10));
+    } else {
+        v[0] = pk(__ldg(src + zo + c.o00), __ldg(src + zo + c.o01));
+        v[1] = pk(__ldg(src + zo + c.o10), __ldg(src + zo + c.o11));
+    }
+}
+
+template <int T, int R>
+__device__ __forceinline__ void h3p_iter(f2 (&L)[T][3][2], f2 (&nxt)[2], f2 (*S)[RY][RX / 2],
+                                         const float *__restrict__ src, float *__restrict__ dst,
+                                         const Cols &c, int lane, int wr, int wru, int wrd, int &zl,
+                                         int nz, size_t plane, bool more, int zout, int z0, int z1,
+                                         bool ox0, bool ox1, bool oy0, bool oy1, f2 r2, f2 m6) {
+    constexpr int P = R % 3, M = (R + 1) % 3, N = (R + 2) % 3;
+    L[0][P][0] = nxt[0];
+    L[0][P][1] = nxt[1];
+    if (more) {
+        zl = zl + 1 < nz ? zl + 1 : zl + 1 - nz;
+        load2x2(nxt, src, (size_t)zl * plane, c);
+    }
+    S[0][wr][lane] = L[0][N][0];
+    S[0][wr + 1][lane] = L[0][N][1];
+    __syncthreads();
+    f2 out[2];
+#pragma unroll
+    for (int t = T - 1; t >= 0; t--) {
+        const int a = t == 0 ? M : P, b = t == 0 ? N : M, d = t == 0 ? P : N;
+        const f2 A = L[t][b][0], B = L[t][b][1];  // rows ry and ry+1 of the middle plane
+        const f2 up = S[t][wru][lane], dn = S[t][wrd][lane];
+        const float l0 = __shfl_up_sync(0xffffffffu, hi_of(A), 1);
+        const float r0 = __shfl_down_sync(0xffffffffu, lo_of(A), 1);
+        const float l1 = __shfl_up_sync(0xffffffffu, hi_of(B), 1);
+        const float r1 = __shfl_down_sync(0xffffffffu, lo_of(B), 1);
+        const f2 vA = ftcs7x2(A, pk(l0, lo_of(A)), pk(hi_of(A), r0), up, B, L[t][a][0],
+                              L[t][d][0], r2, m6);
+        const f2 vB = ftcs7x2(B, pk(l1, lo_of(B)), pk(hi_of(B), r1), A, dn, L[t][a][1],
+                              L[t][d][1], r2, m6);
+        if (t == T - 1) {
+            out[0] = vA;
+            out[1] = vB;
+        } else {
+            L[t + 1][P][0] = vA;
+            L[t + 1][P][1] = vB;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 1; t < T; t++) {
+        S[t][wr][lane] = L[t][N][0];
+        S[t][wr + 1][lane] = L[t][N][1];
+    }
+    if (zout >= z0 && zout < z1) {
+        float *d = dst + (size_t)zout * plane;
+        if (c.pair && ox0 && ox1) {
+            if (oy0) *reinterpret_cast<f2 *>(d + c.o00) = out[0];
+            if (oy1) *reinterpret_cast<f2 *>(d + c.o10) = out[1];
+        } else {
+            if (oy0 && ox0) d[c.o00] = lo_of(out[0]);
+            if (oy0 && ox1) d[c.o01] = hi_of(out[0]);
+            if (oy1 && ox0) d[c.o10] = lo_of(out[1]);
+            if (oy1 && ox1) d[c.o11] = hi_of(out[1]);
+        }
+    }
+}
+
+}  // namespace
+
+template <int T>
+__global__ void __launch_bounds__(NT, 1)
+    k_heat3d_pk(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
+                float r, int zchunk) {
+    constexpr int BX = RX - 2 * T, BY = RY - 2 * T;
+    __shared__ __align__(16) f2 S[T][RY][RX / 2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles_x = (nx + BX - 1) / BX, tiles_y = (ny + BY - 1) / BY;
+    const int nchunks = (nz + zchunk - 1) / zchunk;
+    const int nblk = tiles_x * tiles_y * nchunks;
+    const int rx = 2 * lane, ry = 2 * warp;
+    const int ryu = ry > 0 ? ry - 1 : 0, ryd = ry + 2 < RY ? ry + 2 : RY - 1;
+    const size_t plane = (size_t)ny * nx;
+    const f2 r2 = pk(r, r), m6 = pk(-6.0f, -6.0f);
+
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int tx = b % tiles_x, ty = (b / tiles_x) % tiles_y, ch = b / (tiles_x * tiles_y);
+        const int x0 = tx * BX - T, y0 = ty * BY - T;
+        const int z0 = ch * zchunk, z1 = min(nz, z0 + zchunk);
+        const int gx0 = wrapi(x0 + rx, nx), gx1 = wrapi(x0 + rx + 1, nx);
+        const int gy0 = wrapi(y0 + ry, ny), gy1 = wrapi(y0 + ry + 1, ny);
+        const bool ox0 = rx >= T && rx < RX - T && x0 + rx < nx;
+        const bool ox1 = rx + 1 >= T && rx + 1 < RX - T && x0 + rx + 1 < nx;
+        const bool oy0 = ry >= T && ry < RY - T && y0 + ry < ny;
+        const bool oy1 = ry + 1 >= T && ry + 1 < RY - T && y0 + ry + 1 < ny;
+        Cols c;
+        c.o00 = (size_t)gy0 * nx + gx0;
+        c.o01 = (size_t)gy0 * nx + gx1;
+        c.o10 = (size_t)gy1 * nx + gx0;
+        c.o11 = (size_t)gy1 * nx + gx1;
+        c.pair = gx1 == gx0 + 1 && (gx0 & 1) == 0 && (nx & 1) == 0;
+
+        f2 L[T][3][2];
+#pragma unroll
+        for (int t = 0; t < T; t++)
+#pragma unroll
+            for (int s = 0; s < 3; s++) L[t][s][0] = L[t][s][1] = 0ull;
+
+        const int iters = (z1 - z0) + 3 * T - 1;
+        int zl = wrapi(z0 - T, nz);
+        f2 nxt[2];
+        load2x2(nxt, src, (size_t)zl * plane, c);
+        const int zout = z0 - 3 * T + 1;
+        for (int i = 0; i < iters; i += 3) {
+            h3p_iter<T, 0>(L, nxt, S, src, dst, c, lane, ry, ryu, ryd, zl, nz, plane,
+                           i + 1 < iters, zout + i, z0, z1, ox0, ox1, oy0, oy1, r2, m6);
+            if (i + 1 >= iters) break;
+            h3p_iter<T, 1>(L, nxt, S, src, dst, c, lane, ry, ryu, ryd, zl, nz, plane,
+                           i + 2 < iters, zout + i + 1, z0, z1, ox0, ox1, oy0, oy1, r2, m6);
+            if (i + 2 >= iters) break;
+            h3p_iter<T, 2>(L, nxt, S, src, dst, c, lane, ry, ryu, ryd, zl, nz, plane,
+                           i + 3 < iters, zout + i + 2, z0, z1, ox0, ox1, oy0, oy1, r2, m6);
+        }
+        __syncthreads();
+    }
+}
+
 int heat3d_blocks(int nz, int ny, int nx, int T, int zchunk) {
     const int BX = RX - 2 * T, BY = RY - 2 * T;
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + zchunk - 1) / zchunk);
@@ -346,6 +509,15 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
     const int blocks = heat3d_blocks(nz, ny, nx, steps, zchunk);
     unsigned g = cfg ? cfg->grid[0] * cfg->grid[1] * cfg->grid[2] : (unsigned)blocks;
     if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != NT) return cudaErrorInvalidValue;
+    if (tune::get("heat3d.variant") == 2) {
+        switch (steps) {
+            case 1: k_heat3d_pk<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+            case 2: k_heat3d_pk<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+            case 3: k_heat3d_pk<3><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+            case 4: k_heat3d_pk<4><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        }
+        return cudaGetLastError();
+    }
     if (tune::get("heat3d.variant") == 1) {
         switch (steps) {
             case 1: k_heat3d_rot<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;

@@ -70,15 +70,16 @@ def test_heat3d_bitexact_across_blocking(dev):
 
 @pytest.mark.parametrize("shape", [(40, 72, 96), (9, 70, 131), (8, 8, 8), (21, 33, 64)])
 def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
-    """Both forms of the 3D kernel (plane registers copied or rotated) and
-    every z split give the bits of one plain step per launch; odd nx takes
-    the scalar-load path of the rotated form, small nz the wrapped z index."""
+    """Every form of the 3D kernel (plane registers copied, rotated, rotated
+    with paired FP32 instructions) and every z split give the bits of one
+    plain step per launch of the default form; odd nx takes the scalar-load
+    path, small nz the wrapped z index."""
     u0 = synth.heat3d_input(shape[2], seed=330 + shape[0], nz=shape[0], ny=shape[1])
     ref, _ = run3d(dev, u0, 9, "plain", 1)
     want = oracle.heat3d(u0.astype(np.float64), float(R), 9)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.zchunks")}
     try:
-        for variant in (0, 1):
+        for variant in (0, 1, 2):
             hxc.tune_set("heat3d.variant", variant)
             for nch in (0, 1, 3):
                 hxc.tune_set("heat3d.zchunks", nch)
