@@ -401,6 +401,7 @@ def secondary(dev, timer, peaks):
     res["gradient_over_forward_time"] = res["fused"]["ms"] / res["forward"]["ms"]
     out["adjoint_2048^2_500steps_f64"] = res
     del b0, bkr, bkk, tgt, uT, lam, lb, gk, gu
+    out["heat2d_streamed_8192_64tiles_f64"] = stream2d_bench(dev)
     out["partition_alg1_p4_f64"] = partition_bench(dev, timer)
     out["mandelbrot_png_f32"] = mandelbrot_bench(dev, timer)
     return out
@@ -485,6 +486,51 @@ def mandelbrot_bench(dev, timer, sides=(1024, 2048, 4096, 8192), frames=8, max_i
         shutil.rmtree(tmp, ignore_errors=True)
 
 
+def link_peak(dev, host_in, host_out, buf_in, buf_out, reps=4):
+    """The host link alone: host_in copied to the device and buf_out copied to
+    host_out at the same time (one copy each way, two stream slots); GB/s of
+    both directions together, median of the repetitions after the first."""
+    import time
+    from paper_1810_11482_b300 import hxc
+    ms = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fw = buf_in.write(host_in, slot=0)
+        fr = buf_out.read(host_out, slot=1)
+        assert hxc.wait_all([fw, fr]) == hxc.HXC_OK
+        ms.append((time.perf_counter() - t0) * 1e3)
+    return (host_in.nbytes + host_out.nbytes) / (float(np.median(ms[1:])) / 1e3) / 1e9
+
+
+def stream2d_bench(dev, n=8192, tiles=(8, 8), steps=6):
+    """The 2D run streamed through the device every step (host-resident
+    field, Algorithm 1 per step): host-clock time per step of the
+    asynchronous tile futures and of the native sequential loop, and the host
+    link throughput against the link measured alone."""
+    import time
+    from paper_1810_11482_b300 import hxc, synth
+    a, b = hxc.host_empty((n, n)), hxc.host_empty((n, n))
+    a[:] = synth.bumps2d(n, n, seed=2)
+    res = {"field": [n, n], "tiles": list(tiles), "steps": steps}
+    for seq in (False, True):
+        hxc.heat2d_stream_run(dev, a, b, tiles, R2D, 2, seq)[0].get()
+        t0 = time.perf_counter()
+        f, st, _ = hxc.heat2d_stream_run(dev, a, b, tiles, R2D, steps, seq)
+        f.get()
+        ms = (time.perf_counter() - t0) * 1e3 / steps
+        key = "sequential" if seq else "futures"
+        res[key] = {"ms_per_step": ms, "updates_per_s": n * n / (ms / 1e3),
+                    "host_link_gbs": (st.h2d_bytes + st.d2h_bytes) / steps / (ms / 1e3) / 1e9}
+    res["futures_speedup"] = res["sequential"]["ms_per_step"] / res["futures"]["ms_per_step"]
+    bi, bo = dev.buffer(a.nbytes), dev.buffer(a.nbytes)
+    peak = link_peak(dev, a, b, bi, bo)
+    ach = res["futures"]["host_link_gbs"]
+    res["roofline"] = {"bound": "host link", "achieved": ach, "peak": peak, "unit": "GB/s",
+                       "frac": ach / peak,
+                       "peak_source": "measured here: the field in and out concurrently"}
+    return res
+
+
 def partition_bench(dev, timer, ms_exp=range(1, 9), parts=4):
     """Sec. 5.1.2 (Algorithm 1): host-clock time of the three loops (copy in,
     kernel, copy out, per partition) until the results are on the host, on
@@ -534,17 +580,8 @@ def partition_bench(dev, timer, ms_exp=range(1, 9), parts=4):
             kms.append(timer.stop(hxc.when_all(fs)))
         res["kernels_only_ms"] = float(np.median(kms))
         rows.append(res)
-    # the host link alone: the whole largest vector in and out at the same time
-    # (one copy each way on two stream slots), the bound of Algorithm 1
     n = nmax
-    link = []
-    for _ in range(4):
-        t0 = time.perf_counter()
-        fw = work.write(x_all, slot=0)
-        fr = side.read(r_all, slot=1)
-        assert hxc.wait_all([fw, fr]) == hxc.HXC_OK
-        link.append((time.perf_counter() - t0) * 1e3)
-    link_gbs = 16.0 * n / (float(np.median(link[1:])) / 1e3) / 1e9
+    link_gbs = link_peak(dev, x_all, r_all, work, side)
     last = rows[-1]
     return {"sizes": rows,
             "roofline": {"bound": "host link", "achieved": last["host_link_gbs"], "peak": link_gbs,

@@ -455,6 +455,25 @@ hxc_status hxc_heat2d_run_host(hxc_device dev, const double *host_u0, double *ho
  * `steps_per_launch` (1..4, 0 = 4) steps per launch with temporal blocking,
  * GRAPH captures the fused launches once and replays them.  All modes give
  * bit-identical results. */
+/* The 2D run with the field in host memory and every step streamed through
+ * the device (Algorithm 1 per step; the contrast Sec. 5.1.1 measures):
+ * each of the tiles_y x tiles_x tiles (split as in hxc_heat2d_run) is copied
+ * in with its one-cell halo, advanced one step and copied back, every step.
+ * host_a holds the initial ny x nx field; host_b is the second host array
+ * (the arrays alternate: after `steps` steps the result is in host_a if
+ * steps is even, in host_b if odd; both are overwritten).  Both should be
+ * page-locked (hxc_host_alloc) for copies to overlap.  sequential = 0:
+ * every tile-step is a future on the tile's stream slot, after the
+ * tile-steps of the previous step whose results its halo reads, so copies
+ * and kernels of different tiles overlap; *out completes when the last
+ * tile is back.  sequential != 0: the native sequential loop (copy in,
+ * kernel, copy out, wait, tile after tile) on one stream; returns when done
+ * with *out ready.  Results are bit-identical to hxc_heat2d_run. */
+hxc_status hxc_heat2d_stream_run(hxc_device dev, double *host_a, double *host_b, int64_t ny,
+                                 int64_t nx, int64_t tiles_y, int64_t tiles_x, double r, int steps,
+                                 int sequential, const hxc_future *deps, int ndeps,
+                                 hxc_future *out, hxc_run_stats *stats);
+
 hxc_status hxc_heat3d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, int64_t nz, int64_t ny,
                           int64_t nx, float r, int steps, hxc_mode mode, int steps_per_launch,
                           const hxc_future *deps, int ndeps, hxc_future *out,

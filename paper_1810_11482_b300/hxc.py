@@ -212,6 +212,10 @@ _SIGS = {
     "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
                                        ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_heat2d_stream_run": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, i64, i64, i64,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut),
+                                     ctypes.POINTER(hxc_run_stats)]),
     "hxc_partition_run": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, ctypes.c_int, c_buf,
                                  ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut)]),
     "hxc_partition_run_native": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, ctypes.c_int,
@@ -587,6 +591,25 @@ def _f64_host(a, what):
     if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
         raise ValueError(what + " must be a C-contiguous float64 array")
     return a.ctypes.data
+
+
+def heat2d_stream_run(dev, host_a, host_b, tiles, r, steps, sequential=False, deps=()):
+    """hxc_heat2d_stream_run on two (ny, nx) float64 host arrays; returns
+    (future, stats, result array) -- the result is host_a after an even
+    number of steps, host_b after an odd one."""
+    if host_a.shape != host_b.shape or host_a.ndim != 2:
+        raise ValueError("host_a and host_b must be (ny, nx) arrays of the same shape")
+    ny, nx = host_a.shape
+    arr, n = _futs(deps)
+    out = c_fut()
+    st = hxc_run_stats()
+    check(lib().hxc_heat2d_stream_run(dev.h, _f64_host(host_a, "host_a"), _f64_host(host_b, "host_b"),
+                                      ny, nx, tiles[0], tiles[1], r, steps, int(bool(sequential)),
+                                      arr, n, ctypes.byref(out), ctypes.byref(st)),
+          "heat2d_stream_run")
+    f = Future(out.value)
+    f._host = (host_a, host_b)
+    return f, st, (host_a if steps % 2 == 0 else host_b)
 
 
 def partition_run(dev, host_x, host_r, parts, work, deps=()):
