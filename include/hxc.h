@@ -455,6 +455,13 @@ hxc_status hxc_heat2d_run_host(hxc_device dev, const double *host_u0, double *ho
  * `steps_per_launch` (1..4, 0 = 4) steps per launch with temporal blocking,
  * GRAPH captures the fused launches once and replays them.  All modes give
  * bit-identical results. */
+/* The host half of the norms (a then-continuation of every snapshot in
+ * hxc_heat2d_run) as a call of its own: out[i] = sqrt(sum of squares) of
+ * the counts[i] doubles at arrays[i], one task per array on the worker
+ * pool, in the same summation order as the run's continuations (blocks of
+ * 1024 squares over 8 accumulators, block sums pairwise).  Synchronous. */
+hxc_status hxc_host_norms(const double *const *arrays, const int64_t *counts, int n, double *out);
+
 /* The 2D run with the field in host memory and every step streamed through
  * the device (Algorithm 1 per step; the contrast Sec. 5.1.1 measures):
  * each of the tiles_y x tiles_x tiles (split as in hxc_heat2d_run) is copied

@@ -924,6 +924,33 @@ hxc_status hxc_heat2d_run_host(hxc_device dh, const double *host_u0, double *hos
 }
 
 
+hxc_status hxc_host_norms(const double *const *arrays, const int64_t *counts, int n, double *out) {
+    if (n < 0 || (n > 0 && (!arrays || !counts || !out))) {
+        set_error("hxc_host_norms: NULL argument");
+        return HXC_E_INVALID;
+    }
+    for (int i = 0; i < n; i++)
+        if (counts[i] < 0 || (counts[i] > 0 && !arrays[i])) {
+            set_error("hxc_host_norms: array %d is invalid", i);
+            return HXC_E_INVALID;
+        }
+    std::vector<HostNormTask> tasks(n);
+    std::vector<FutRef> done(n);
+    for (int i = 0; i < n; i++) {
+        tasks[i] = HostNormTask{arrays[i], counts[i], out + i};
+        done[i] = make_pending();
+        HostNormTask *t = &tasks[i];
+        FutRef r = done[i];
+        pool().submit([t, r] { fut_set_done(r, host_norm_fn(t)); });
+    }
+    hxc_status st = HXC_OK;
+    for (auto &f : done) {
+        hxc_status s2 = fut_wait(f, -1);
+        if (!st) st = s2;
+    }
+    return st;
+}
+
 hxc_status hxc_heat3d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t nz, int64_t ny,
                           int64_t nx, float r, int steps, hxc_mode mode, int steps_per_launch,
                           const hxc_future *deps, int ndeps, hxc_future *out,

@@ -212,6 +212,8 @@ _SIGS = {
     "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
                                        ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_host_norms": (c_st, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(i64), ctypes.c_int,
+                              ctypes.c_void_p]),
     "hxc_heat2d_stream_run": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, i64, i64, i64,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut),
@@ -591,6 +593,16 @@ def _f64_host(a, what):
     if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
         raise ValueError(what + " must be a C-contiguous float64 array")
     return a.ctypes.data
+
+
+def host_norms(arrays):
+    """sqrt(sum v^2) of each float64 array on the host worker pool."""
+    arrays = [np.ascontiguousarray(a, dtype=np.float64) for a in arrays]
+    ptrs = (ctypes.c_void_p * max(1, len(arrays)))(*[a.ctypes.data for a in arrays])
+    counts = (i64 * max(1, len(arrays)))(*[a.size for a in arrays])
+    out = np.empty(len(arrays))
+    check(lib().hxc_host_norms(ptrs, counts, len(arrays), out.ctypes.data), "host_norms")
+    return out
 
 
 def heat2d_stream_run(dev, host_a, host_b, tiles, r, steps, sequential=False, deps=()):

@@ -10,9 +10,10 @@ import tempfile
 import threading
 import time
 
+import numpy as np
 import pytest
 
-from paper_1810_11482_b300 import hxc
+from paper_1810_11482_b300 import hxc, synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
@@ -241,3 +242,16 @@ def test_program_calls_reject_bad_handles():
     n = ctypes.c_size_t()
     assert L.hxc_program_build_log(None, None, 0, ctypes.byref(n)) == hxc.HXC_E_INVALID
     assert L.hxc_program_release(None) == hxc.HXC_E_INVALID
+
+
+def test_host_norms_on_the_worker_pool():
+    """hxc_host_norms needs no device: against a long-double sum, on empty,
+    short, ragged and long arrays."""
+    arrays = [np.zeros(0), np.array([3.0, 4.0]), synth.uniform(50, 1025, lo=-1, hi=1),
+              synth.uniform(51, 1 << 20, lo=-2, hi=2), synth.uniform(52, 8191)]
+    got = hxc.host_norms(arrays)
+    want = [float(np.sqrt(np.sum(a.astype(np.longdouble) ** 2))) for a in arrays]
+    assert got[0] == 0.0 and got[1] == 5.0
+    assert np.max(np.abs(got[2:] - want[2:]) / np.array(want[2:])) <= 2e-14
+    L = hxc.lib()
+    assert L.hxc_host_norms(None, None, 2, None) == hxc.HXC_E_INVALID
