@@ -340,6 +340,12 @@ def ours(args, world, rank, local, pg):
     return out
 
 
+def fp64_roof(ops, ms, peaks, what):
+    ach = ops / (ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peaks["fp64_gops"], "unit": "Gop/s",
+            "frac": ach / peaks["fp64_gops"], "count": what}
+
+
 def secondary(dev, timer, peaks):
     """The other workloads of the path, each in every launch mode on the same
     GPU: updates/s per mode and the speed-up over the plain per-partition
@@ -372,6 +378,8 @@ def secondary(dev, timer, peaks):
                                                          deps=[d] if d else ())[0], reps=5, warm=2)
         res[mode] = {"ms": ms, "updates_per_s": n * st1 / (ms / 1e3)}
     speedups(res)
+    res["roofline"] = fp64_roof(3 * n * st1, res["graph"]["ms"], peaks,
+                                "3 FP64 operations per update, graph mode")
     out["heat1d_2^20_8parts_100steps_f64"] = res
 
     # 3D periodic FP32 512^3, r = 0.15, 200 steps, 4 steps per launch
@@ -411,6 +419,8 @@ def secondary(dev, timer, peaks):
     speedups(res)
     res["bitwise_equal_modes"] = bool(all(np.array_equal(outs["plain"], outs[m]) for m in outs))
     res["points"] = int(total)
+    res["roofline"] = fp64_roof(5 * total * 50, res["fused"]["ms"], peaks,
+                                "5 FP64 operations per update (coefficient form), fused mode")
     out["batch_4096_problems_50steps_f64"] = res
     del kap, ub
 
@@ -437,6 +447,11 @@ def secondary(dev, timer, peaks):
         res[mode] = {"ms": ms, "gradient_updates_per_s": n2 * n2 * st4 / (ms / 1e3)}
     speedups(res)
     res["gradient_over_forward_time"] = res["fused"]["ms"] / res["forward"]["ms"]
+    res["roofline"] = fp64_roof(29 * n2 * n2 * st4, res["fused"]["ms"], peaks,
+                                "29 FP64 operations per cell-step: forward with checkpoints 5, "
+                                "segment recompute 5, adjoint step 5, kappa-gradient 14; fused")
+    res["forward"]["roofline"] = fp64_roof(5 * n2 * n2 * st4, res["forward"]["ms"], peaks,
+                                           "5 FP64 operations per update")
     out["adjoint_2048^2_500steps_f64"] = res
     del b0, bkr, bkk, tgt, uT, lam, lb, gk, gu
     out["heat2d_streamed_8192_64tiles_f64"] = stream2d_bench(dev)
