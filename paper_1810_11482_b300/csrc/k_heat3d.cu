@@ -17,6 +17,7 @@
 // iteration), so level t runs 2t planes behind level 0.  Cells within
 // distance t of the region edge are wrong at level t and are never written:
 // only the central (RX-2T) x (RY-2T) columns of level T are stored.
+#include "f32x2.cuh"
 #include "kernels.cuh"
 #include "tune.hpp"
 
@@ -313,31 +314,11 @@ __global__ void __launch_bounds__(NT, 1)
 // ---------------------------------------------------------------------------
 // Variant 2: variant 1 with the arithmetic on packed pairs.  The two
 // x-adjacent cells of each of the thread's rows are held as one 64-bit pair
-// and updated with the paired FP32 instructions of sm_100-class GPUs
-// (add.rn.f32x2, fma.rn.f32x2), which round each half exactly as the scalar
-// instruction does: the canonical expression, evaluated on two cells per
+// (the low half the lower x) and updated with the paired FP32 instructions
+// (f32x2.cuh): the canonical expression, evaluated on two cells per
 // instruction.
 namespace {
 
-typedef unsigned long long f2;  // two floats; the low half is the lower x
-
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float lo_of(f2 v) { return __uint_as_float((unsigned)v); }
-__device__ __forceinline__ float hi_of(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 // ftcs7 on two cells at once (same operation order and rounding)
 __device__ __forceinline__ f2 ftcs7x2(f2 u, f2 xm, f2 xp, f2 ym, f2 yp, f2 zm, f2 zp, f2 r2,
                                       f2 m6) {
