@@ -259,8 +259,14 @@ __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__
         Vec<V> prv, cur, nxt;
         load_row<V>(prv, src, ny, nx, ys - 1, xl, active);
         load_row<V>(cur, src, ny, nx, ys, xl, active);
+        // the strip's outside neighbours (lane 0's left, the last lane's
+        // right), loaded one row ahead like the rows themselves
+        double eL = lane == 0 ? at2(src, ny, nx, ys, xs - 1) : 0.0;
+        double eR = last ? at2(src, ny, nx, ys, xl + V) : 0.0;
         for (int64_t y = ys; y < ye; y++) {
             load_row<V>(nxt, src, ny, nx, y + 1, xl, active);
+            const double eLn = lane == 0 && y + 1 < ye ? at2(src, ny, nx, y + 1, xs - 1) : 0.0;
+            const double eRn = last && y + 1 < ye ? at2(src, ny, nx, y + 1, xl + V) : 0.0;
             double hi;
             if constexpr (V == 2)
                 hi = cur.b;
@@ -268,8 +274,10 @@ __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__
                 hi = cur.a;
             double left = __shfl_up_sync(0xffffffffu, hi, 1);
             double right = __shfl_down_sync(0xffffffffu, cur.a, 1);
-            if (lane == 0) left = at2(src, ny, nx, y, xs - 1);
-            if (last) right = at2(src, ny, nx, y, xl + V);
+            if (lane == 0) left = eL;
+            if (last) right = eR;
+            eL = eLn;
+            eR = eRn;
             if (active) {
                 if constexpr (V == 2) {
                     double2 o;
