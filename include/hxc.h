@@ -555,6 +555,8 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
  *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).
+ *   "batch.block"  threads per CTA of the persistent batch kernel: 256 (default),
+ *                  512 or 1024; blocks x CTAs per SM must fit the SM.
  * Returns HXC_E_INVALID for an unknown key. */
 hxc_status hxc_tune_set(const char *key, int64_t value);
 hxc_status hxc_tune_get(const char *key, int64_t *value);

@@ -118,7 +118,7 @@ def tune(quick=False, log=print):
     bu.write(ub).get()
     bk.write(kap).get()
     log("batch")
-    result.update(_search(timer, {"batch.ctas_per_sm": [1, 2, 3, 4]},
+    result.update(_search(timer, {"batch.block": [256, 512], "batch.ctas_per_sm": [1, 2, 3, 4]},
                           lambda d: hxc.varcoef_batch_run(dev, bu, bk, sides, cs, 50, "fused", d)[0],
                           log))
     return dev, result

@@ -236,7 +236,7 @@ struct VcProblem {
 // next one, so the batch is a single launch with no device-wide barrier.
 // The CTA computes the problem's coefficients into wE/wS/m first; steps
 // ping-pong between u and tmp; an odd step count ends with a copy into u.
-__global__ void __launch_bounds__(256) k_vc_batch(const VcProblem *__restrict__ probs, int nprob,
+__global__ void __launch_bounds__(1024) k_vc_batch(const VcProblem *__restrict__ probs, int nprob,
                                                   unsigned *queue, double *u, double *tmp,
                                                   const double *__restrict__ kap, double *wE,
                                                   double *wS, double *m, int steps, Fk f) {
@@ -385,7 +385,8 @@ cudaError_t vc_batch_persistent(const void *probs, int nprob, unsigned *queue, d
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const int g = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : (int)tune::get("batch.ctas_per_sm"));
-    k_vc_batch<<<g, 256, 0, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
+    const int b = (int)tune::get("batch.block");
+    k_vc_batch<<<g, b, 0, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
                                   wE, wS, m, steps, kF);
     return cudaGetLastError();
 }

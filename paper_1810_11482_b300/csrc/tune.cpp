@@ -32,6 +32,7 @@ Knob g_knobs[] = {
     {"heat3d.variant", 2, 0, 2},      // 0 copied planes, 1 rotated, 2 rotated + f32x2
     {"heat1d.tb_ctas", 0, 0, 1 << 16},  // CTAs per partition of the 1D blocked kernel (0: SMs/parts)
     {"batch.ctas_per_sm", 4, 1, 16},  // CTAs per SM of the persistent batch kernel
+    {"batch.block", 256, 256, 1024},  // threads per CTA of the persistent batch kernel
 };
 std::mutex g_m;
 
