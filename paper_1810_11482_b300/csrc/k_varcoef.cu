@@ -385,7 +385,7 @@ cudaError_t vc_batch_persistent(const void *probs, int nprob, unsigned *queue, d
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const int g = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : (int)tune::get("batch.ctas_per_sm"));
-    const int b = (int)tune::get("batch.block");
+    const int b = (int)tune::get("batch.block") / 32 * 32;  // whole warps
     k_vc_batch<<<g, b, 0, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
                                   wE, wS, m, steps, kF);
     return cudaGetLastError();
