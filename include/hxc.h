@@ -547,11 +547,15 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *   "heat2d.rows"  rows each warp of the 2D kernel walks (default 8).
  *   "heat2d.occupancy"  minimum resident 256-thread CTAs per SM the 2D
  *                  kernel is compiled for, 4..6 (default 4).
- *   "heat3d.zchunks"  z chunks of a 3D launch, 0 = fill whole waves.
+ *   "heat3d.zchunks"  z chunks of a 3D launch of forms 0..2, 0 = fill whole
+ *                  waves.
  *   "heat3d.variant"  3D kernel form: 0 = plane registers copied each z
  *                  step, 1 = plane registers rotated (z loop unrolled by 3),
- *                  2 = rotated, arithmetic on paired FP32 instructions
- *                  (default).
+ *                  2 = rotated, arithmetic on paired FP32 instructions,
+ *                  3 = two plane registers per level (centre + partial sum),
+ *                  2 x 4 cells per thread, 64 x 64 regions, the z range split
+ *                  evenly over one CTA per SM (default; a launch with an
+ *                  hxc_launch_cfg still takes 512 threads per CTA and any grid).
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
  *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).

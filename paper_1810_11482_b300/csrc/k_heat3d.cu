@@ -1,7 +1,7 @@
 // 3D 7-point FTCS, FP32, periodic, T (1..4) fused steps per launch.
 //
 // Canonical arithmetic (every variant, every T):
-//   s  = ((u[x-1] + u[x+1]) + (u[y-1] + u[y+1])) + (u[z-1] + u[z+1])
+//   s  = (((u[x-1] + u[x+1]) + (u[y-1] + u[y+1])) + u[z-1]) + u[z+1]
 //   t  = fma(-6, u, s);   u' = fma(r, t, u)            (FP32, round-to-nearest)
 // so T fused steps give the same bits as T single-step launches.
 //
@@ -17,6 +17,8 @@
 // iteration), so level t runs 2t planes behind level 0.  Cells within
 // distance t of the region edge are wrong at level t and are never written:
 // only the central (RX-2T) x (RY-2T) columns of level T are stored.
+#include <algorithm>
+
 #include "f32x2.cuh"
 #include "kernels.cuh"
 #include "tune.hpp"
@@ -29,7 +31,7 @@ constexpr int RX = 64, RY = 32, NT = 512;
 
 __device__ __forceinline__ float ftcs7(float u, float xm, float xp, float ym, float yp, float zm,
                                        float zp, float r) {
-    float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+    float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), zm), zp);
     float t = __fmaf_rn(-6.0f, u, s);
     return __fmaf_rn(r, t, u);
 }
@@ -322,7 +324,7 @@ namespace {
 // ftcs7 on two cells at once (same operation order and rounding)
 __device__ __forceinline__ f2 ftcs7x2(f2 u, f2 xm, f2 xp, f2 ym, f2 yp, f2 zm, f2 zp, f2 r2,
                                       f2 m6) {
-    const f2 s = add2(add2(add2(xm, xp), add2(ym, yp)), add2(zm, zp));
+    const f2 s = add2(add2(add2(add2(xm, xp), add2(ym, yp)), zm), zp);
     return fma2(r2, fma2(m6, u, s), u);
 }
 
@@ -454,6 +456,187 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Variant 3: two values per cell and level instead of three, 2 x 4 cells per
+// thread, and the z range split evenly over the CTAs.
+//
+// A level keeps, per cell, its centre plane c and the partial sum
+// p = (x-pair + y-pair) + (plane below c), formed as soon as c arrives; when
+// the plane above arrives the update is u' = fma(r, fma(-6, c, p + above), c).
+// So a level needs two planes of registers, and the levels chain through
+// registers within one z iteration: the plane level t produces is the plane
+// level t+1 receives in the same iteration (level t+1 lags one plane).
+//
+// A warp covers the 64 columns of its region row band as 32 lanes x 2
+// adjacent columns (one paired-FP32 register per row) and 4 rows, so 16
+// warps cover a 64 x 64 region.  x-neighbours outside the thread's pair come
+// from the adjacent lanes by shuffles, y-neighbours inside its 4 rows from its
+// own registers, and only the band's first and last rows go through shared
+// memory (double-buffered, one barrier per z iteration).
+//
+// Work: the (region, output plane) pairs are numbered region-major and every
+// CTA takes an equal contiguous share, so the CTAs finish together; each
+// region segment of a share costs 2T extra iterations to fill the level chain.
+namespace {
+
+constexpr int V3_NW = 16, V3_H = 4 * V3_NW;  // warps per CTA, region rows
+
+// the thread's two columns of one row (one 8-byte load when adjacent and aligned)
+__device__ __forceinline__ f2 ld_pair(const float *__restrict__ p, unsigned a0, unsigned a1,
+                                      bool pair) {
+    if (pair) return __ldg(reinterpret_cast<const unsigned long long *>(p + a0));
+    return pk(__ldg(p + a0), __ldg(p + a1));
+}
+
+// One z iteration.  Q selects which of X / Y holds the centre planes (the
+// other receives the incoming planes and becomes the centre).
+template <int T, int Q>
+__device__ __forceinline__ void v3_iter(f2 (&X)[T][4], f2 (&Y)[T][4], f2 (&Pp)[T][4],
+                                        f2 (&nxt)[4], f2 *__restrict__ Sb,
+                                        const float *__restrict__ src, float *__restrict__ dst,
+                                        const unsigned (&row)[4], unsigned gx0, unsigned gx1,
+                                        bool pair, int &zl, int nz, size_t plane, bool more,
+                                        bool store, int zout, unsigned omask, int lane, int warp,
+                                        int wu, int wd, f2 r2, f2 m6) {
+    f2(&C)[T][4] = Q ? Y : X;
+    f2(&N)[T][4] = Q ? X : Y;
+    // level 0 receives the prefetched plane; fetch the next one
+#pragma unroll
+    for (int k = 0; k < 4; k++) N[0][k] = nxt[k];
+    if (more) {
+        zl = zl + 1 < nz ? zl + 1 : 0;
+        const float *p = src + (size_t)zl * plane;
+#pragma unroll
+        for (int k = 0; k < 4; k++) nxt[k] = ld_pair(p, row[k] + gx0, row[k] + gx1, pair);
+    }
+    // step 1: every level finishes the cells of its centre plane; the result
+    // is the incoming plane of the next level (level T's is stored)
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const f2 v = fma2(r2, fma2(m6, C[t][k], add2(Pp[t][k], N[t][k])), C[t][k]);
+            if (t + 1 < T) N[t + 1][k] = v;
+            if (t + 1 == T && store) {
+                float *d = dst + (size_t)zout * plane;
+                const unsigned m = omask >> (2 * k);
+                if (pair && (m & 3u) == 3u) {
+                    *reinterpret_cast<f2 *>(d + row[k] + gx0) = v;
+                } else {
+                    if (m & 1u) d[row[k] + gx0] = lo_of(v);
+                    if (m & 2u) d[row[k] + gx1] = hi_of(v);
+                }
+            }
+        }
+    }
+    // step 2: publish the band edge rows of every incoming plane, then form
+    // the partial sums of the new centre planes
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        Sb[((t * V3_NW + warp) * 2 + 0) * 32 + lane] = N[t][0];
+        Sb[((t * V3_NW + warp) * 2 + 1) * 32 + lane] = N[t][3];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        const f2 up = Sb[((t * V3_NW + wu) * 2 + 1) * 32 + lane];
+        const f2 dn = Sb[((t * V3_NW + wd) * 2 + 0) * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const f2 v = N[t][k];
+            const float lft = __shfl_up_sync(0xffffffffu, hi_of(v), 1);
+            const float rgt = __shfl_down_sync(0xffffffffu, lo_of(v), 1);
+            // left cell: (left lane's high) + own high; right cell: own low + (right lane's low)
+            const f2 xs = pk(__fadd_rn(lft, hi_of(v)), __fadd_rn(lo_of(v), rgt));
+            const f2 ys = add2(k == 0 ? up : N[t][k - 1], k == 3 ? dn : N[t][k + 1]);
+            Pp[t][k] = add2(add2(xs, ys), C[t][k]);
+        }
+    }
+}
+}  // namespace
+
+template <int T>
+__global__ void __launch_bounds__(V3_NW * 32, 1)
+    k_heat3d_v3(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
+                float r) {
+    constexpr int BX = 64 - 2 * T, BY = V3_H - 2 * T;
+    extern __shared__ __align__(16) f2 v3_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wu = warp > 0 ? warp - 1 : 0, wd = warp + 1 < V3_NW ? warp + 1 : V3_NW - 1;
+    const int tiles_x = (nx + BX - 1) / BX, tiles_y = (ny + BY - 1) / BY;
+    const int64_t work = (int64_t)tiles_x * tiles_y * nz;
+    const int64_t w_end = work * (blockIdx.x + 1) / gridDim.x;
+    const size_t plane = (size_t)ny * nx;
+    const f2 r2 = pk(r, r), m6 = pk(-6.0f, -6.0f);
+    constexpr int SB = T * V3_NW * 2 * 32;  // f2 per shared buffer
+    int buf = 0;
+
+    for (int64_t w = work * blockIdx.x / gridDim.x; w < w_end;) {
+        const int64_t reg = w / nz;
+        const int za = (int)(w - reg * nz);
+        const int zb = (int)min((int64_t)nz, za + (w_end - w));
+        w += zb - za;
+        const int tx = (int)(reg % tiles_x), ty = (int)(reg / tiles_x);
+        const int x0 = tx * BX - T, y0 = ty * BY - T;
+        const int c0 = 2 * lane;
+        const unsigned gx0 = wrapi(x0 + c0, nx), gx1 = wrapi(x0 + c0 + 1, nx);
+        const bool pair = gx1 == gx0 + 1 && (gx0 & 1u) == 0 && (nx & 1) == 0;
+        const bool ox0 = c0 >= T && c0 < 64 - T && x0 + c0 < nx;
+        const bool ox1 = c0 + 1 >= T && c0 + 1 < 64 - T && x0 + c0 + 1 < nx;
+        unsigned row[4], omask = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int q = 4 * warp + k;
+            row[k] = (unsigned)wrapi(y0 + q, ny) * (unsigned)nx;
+            const bool oy = q >= T && q < V3_H - T && y0 + q < ny;
+            omask |= (oy && ox0 ? 1u : 0u) << (2 * k);
+            omask |= (oy && ox1 ? 2u : 0u) << (2 * k);
+        }
+
+        f2 X[T][4], Y[T][4], Pp[T][4];
+#pragma unroll
+        for (int t = 0; t < T; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) X[t][k] = Y[t][k] = Pp[t][k] = 0ull;
+        // iteration j receives level-0 plane za - T + j and emits level-T
+        // plane za - 2T + j (stored for j >= 2T)
+        const int iters = (zb - za) + 2 * T;
+        int zl = wrapi(za - T, nz);
+        f2 nxt[4];
+        {
+            const float *p = src + (size_t)zl * plane;
+#pragma unroll
+            for (int k = 0; k < 4; k++) nxt[k] = ld_pair(p, row[k] + gx0, row[k] + gx1, pair);
+        }
+        for (int j = 0; j < iters; j += 2) {
+            v3_iter<T, 0>(X, Y, Pp, nxt, v3_smem + buf * SB, src, dst, row, gx0, gx1, pair, zl, nz,
+                          plane, j + 1 < iters, j >= 2 * T, za - 2 * T + j, omask, lane, warp, wu,
+                          wd, r2, m6);
+            buf ^= 1;
+            if (j + 1 >= iters) break;
+            v3_iter<T, 1>(X, Y, Pp, nxt, v3_smem + buf * SB, src, dst, row, gx0, gx1, pair, zl, nz,
+                          plane, j + 2 < iters, j + 1 >= 2 * T, za - 2 * T + j + 1, omask, lane,
+                          warp, wu, wd, r2, m6);
+            buf ^= 1;
+        }
+    }
+}
+
+template <int T>
+cudaError_t v3_launch(unsigned g, const float *src, float *dst, int nz, int ny, int nx, float r,
+                      cudaStream_t s) {
+    constexpr size_t smem = sizeof(f2) * 2 * T * V3_NW * 2 * 32;
+    static bool attr = false;  // idempotent, so a race between first callers is harmless
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_heat3d_v3<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_heat3d_v3<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r);
+    return cudaGetLastError();
+}
+
 int heat3d_blocks(int nz, int ny, int nx, int T, int zchunk) {
     const int BX = RX - 2 * T, BY = RY - 2 * T;
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + zchunk - 1) / zchunk);
@@ -489,8 +672,23 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
     }
     const int blocks = heat3d_blocks(nz, ny, nx, steps, zchunk);
     unsigned g = cfg ? cfg->grid[0] * cfg->grid[1] * cfg->grid[2] : (unsigned)blocks;
+    // variant 3 keeps in-plane offsets in 32 bits; larger planes take variant 2 (same bits)
+    const int64_t variant = tune::get("heat3d.variant");
+    if (variant == 3 && (uint64_t)ny * (uint64_t)nx <= 0xffffffffull) {
+        if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != V3_NW * 32)
+            return cudaErrorInvalidValue;
+        const int BX = 64 - 2 * steps, BY = V3_H - 2 * steps;
+        const int64_t work = (int64_t)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
+        const unsigned g3 = cfg ? g : (unsigned)std::min<int64_t>(sm_count(), work);
+        switch (steps) {
+            case 1: return v3_launch<1>(g3, src, dst, nz, ny, nx, r, s);
+            case 2: return v3_launch<2>(g3, src, dst, nz, ny, nx, r, s);
+            case 3: return v3_launch<3>(g3, src, dst, nz, ny, nx, r, s);
+            case 4: return v3_launch<4>(g3, src, dst, nz, ny, nx, r, s);
+        }
+    }
     if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != NT) return cudaErrorInvalidValue;
-    if (tune::get("heat3d.variant") == 2) {
+    if (variant >= 2) {
         switch (steps) {
             case 1: k_heat3d_pk<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
             case 2: k_heat3d_pk<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
@@ -499,7 +697,7 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
         }
         return cudaGetLastError();
     }
-    if (tune::get("heat3d.variant") == 1) {
+    if (variant == 1) {
         switch (steps) {
             case 1: k_heat3d_rot<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
             case 2: k_heat3d_rot<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;

@@ -61,7 +61,8 @@ def test_heat3d_bitexact_across_blocking(dev):
                       ("graph", 2)):
         got, _ = run3d(dev, u0, 12, mode, spl)
         assert np.array_equal(got, ref), (mode, spl)
-    # x <-> y swap symmetry is exact ((x-pair + y-pair) + z-pair is symmetric in x, y)
+    # x <-> y swap symmetry is exact (((x-pair + y-pair) + z-below) + z-above is
+    # symmetric in x and y)
     sw = np.ascontiguousarray(np.swapaxes(u0, 1, 2)[:, :72, :72])
     a, _ = run3d(dev, sw, 8, "fused", 4)
     b, _ = run3d(dev, np.ascontiguousarray(np.swapaxes(sw, 1, 2)), 8, "fused", 4)
@@ -71,15 +72,16 @@ def test_heat3d_bitexact_across_blocking(dev):
 @pytest.mark.parametrize("shape", [(40, 72, 96), (9, 70, 131), (8, 8, 8), (21, 33, 64)])
 def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     """Every form of the 3D kernel (plane registers copied, rotated, rotated
-    with paired FP32 instructions) and every z split give the bits of one
-    plain step per launch of the default form; odd nx takes the scalar-load
-    path, small nz the wrapped z index."""
+    with paired FP32 instructions, two planes per level with the z range split
+    over the CTAs) and every z split give the bits of one plain step per launch
+    of the default form; odd nx takes the scalar-load path, small nz the
+    wrapped z index."""
     u0 = synth.heat3d_input(shape[2], seed=330 + shape[0], nz=shape[0], ny=shape[1])
     ref, _ = run3d(dev, u0, 9, "plain", 1)
     want = oracle.heat3d(u0.astype(np.float64), float(R), 9)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.zchunks")}
     try:
-        for variant in (0, 1, 2):
+        for variant in (0, 1, 2, 3):
             hxc.tune_set("heat3d.variant", variant)
             for nch in (0, 1, 3):
                 hxc.tune_set("heat3d.zchunks", nch)
@@ -139,3 +141,39 @@ def test_heat3d_product_mode_full_size(dev):
     g = 1.0 - 4.0 * r * sum(math.sin(math.pi * m / n) ** 2 for m in (a, b, c))
     got, _ = run3d(dev, u0, steps, "fused", 4)
     assert np.max(np.abs(got.astype(np.float64) - g ** steps * u0.astype(np.float64))) <= 2e-5
+
+
+@pytest.mark.parametrize("shape", [(33, 200, 130), (5, 64, 64), (70, 57, 250)])
+def test_heat3d_two_plane_form_any_grid(dev, shape):
+    """The two-plane form (variant 3) splits the (region, plane) pairs evenly
+    over whatever grid it is launched with: one CTA, a few CTAs whose shares
+    span several regions, and more CTAs than pairs (empty shares) all give the
+    bits of the copied-plane form (variant 0); 1..4 steps per launch."""
+    u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=340 + shape[0], nz=shape[0],
+                                                 ny=shape[1]), dtype=np.float32)
+    old = hxc.tune_get("heat3d.variant")
+    a, b = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    try:
+        for steps in (1, 2, 3, 4):
+            want = None
+            for variant, grid in ((0, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000)):
+                hxc.tune_set("heat3d.variant", variant)
+                a.write(u0).get()
+                args = hxc.hxc_heat3d_args(a.h, b.h, shape[0], shape[1], shape[2], R, steps)
+                cfg = None if grid is None else hxc.hxc_launch_cfg((grid, 1, 1), (512, 1, 1))
+                dev.launch(hxc.HXC_K_HEAT3D, args, cfg=cfg).get()
+                got = np.empty_like(u0)
+                b.read_sync(got)
+                if want is None:
+                    want = got
+                    ora = oracle.heat3d(u0.astype(np.float64), float(R), steps)
+                    assert relerr(got, ora) <= TOL32
+                else:
+                    assert np.array_equal(got, want), (steps, variant, grid)
+        # a block size other than 512 threads is rejected
+        hxc.tune_set("heat3d.variant", 3)
+        args = hxc.hxc_heat3d_args(a.h, b.h, shape[0], shape[1], shape[2], R, 4)
+        with pytest.raises(hxc.HxcError):
+            dev.launch(hxc.HXC_K_HEAT3D, args, cfg=hxc.hxc_launch_cfg((4, 1, 1), (256, 1, 1))).get()
+    finally:
+        hxc.tune_set("heat3d.variant", old)
