@@ -554,8 +554,10 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *                  2 = rotated, arithmetic on paired FP32 instructions,
  *                  3 = two plane registers per level (centre + partial sum),
  *                  2 x 4 cells per thread, 64 x 64 regions, the z range split
- *                  evenly over one CTA per SM (default; a launch with an
- *                  hxc_launch_cfg still takes 512 threads per CTA and any grid).
+ *                  evenly over one CTA per SM, 4 = form 3 with the input
+ *                  planes copied into a shared-memory ring two planes ahead
+ *                  (default).  Forms 3 and 4 launched with an hxc_launch_cfg
+ *                  take 512 threads per CTA and any grid.
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
  *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).

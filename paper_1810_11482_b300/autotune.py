@@ -97,7 +97,7 @@ def tune(quick=False, log=print):
     a, b = dev.buffer(u3.nbytes), dev.buffer(u3.nbytes)
     a.write(u3).get()
     log("heat3d")
-    result.update(_search(timer, {"heat3d.variant": [0, 1, 2, 3], "heat3d.zchunks": [0, 1, 2, 3, 4, 6, 8]},
+    result.update(_search(timer, {"heat3d.variant": [0, 1, 2, 3, 4], "heat3d.zchunks": [0, 1, 2, 3, 4, 6, 8]},
                           lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 8, "fused", 4, d)[0],
                           log))
     del a, b

@@ -637,6 +637,207 @@ cudaError_t v3_launch(unsigned g, const float *src, float *dst, int nz, int ny, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Variant 4: variant 3 with the level-0 planes copied into a shared-memory
+// ring by cp.async, V4_D planes ahead, instead of loaded into registers one
+// plane ahead.  The ring holds the region's whole plane, so level 0's band
+// edge rows are read from it directly; levels 1..T-1 publish theirs as in
+// variant 3.  A ring slot is refilled two iterations after its last read
+// (V4_D + 2 slots), which the per-iteration barrier orders.
+namespace {
+
+constexpr int V4_D = 2, V4_RS = V4_D + 2;
+
+__device__ __forceinline__ void cp8(void *sdst, const void *gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp4(void *sdst, const void *gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// copy the thread's 4 x 2 cells of plane zq into ring slot `slot`
+__device__ __forceinline__ void v4_fetch(f2 *__restrict__ ring, int slot, const float *__restrict__ p,
+                                         const unsigned (&row)[4], unsigned gx0, unsigned gx1,
+                                         bool pair, int lane, int warp) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        f2 *d = ring + ((size_t)slot * V3_H + 4 * warp + k) * 32 + lane;
+        if (pair) {
+            cp8(d, p + row[k] + gx0);
+        } else {
+            cp4(d, p + row[k] + gx0);
+            cp4(reinterpret_cast<float *>(d) + 1, p + row[k] + gx1);
+        }
+    }
+    cp_commit();
+}
+
+template <int T, int Q>
+__device__ __forceinline__ void v4_iter(f2 (&X)[T][4], f2 (&Y)[T][4], f2 (&Pp)[T][4],
+                                        f2 *__restrict__ ring, int slot, int fslot,
+                                        f2 *__restrict__ Sb, const float *__restrict__ src,
+                                        float *__restrict__ dst, const unsigned (&row)[4],
+                                        unsigned gx0, unsigned gx1, bool pair, int &zf, int nz,
+                                        size_t plane, bool store, int zout, unsigned omask,
+                                        int lane, int warp, int ru, int rd, int wu, int wd, f2 r2,
+                                        f2 m6) {
+    f2(&C)[T][4] = Q ? Y : X;
+    f2(&N)[T][4] = Q ? X : Y;
+    // fetch plane V4_D ahead, then wait for this iteration's plane (own copies)
+    zf = zf + 1 < nz ? zf + 1 : 0;
+    v4_fetch(ring, fslot, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+    cp_wait<V4_D>();
+    const f2 *rs = ring + (size_t)slot * V3_H * 32;
+#pragma unroll
+    for (int k = 0; k < 4; k++) N[0][k] = rs[(4 * warp + k) * 32 + lane];
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const f2 v = fma2(r2, fma2(m6, C[t][k], add2(Pp[t][k], N[t][k])), C[t][k]);
+            if (t + 1 < T) N[t + 1][k] = v;
+            if (t + 1 == T && store) {
+                float *d = dst + (size_t)zout * plane;
+                const unsigned m = omask >> (2 * k);
+                if (pair && (m & 3u) == 3u) {
+                    *reinterpret_cast<f2 *>(d + row[k] + gx0) = v;
+                } else {
+                    if (m & 1u) d[row[k] + gx0] = lo_of(v);
+                    if (m & 2u) d[row[k] + gx1] = hi_of(v);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 1; t < T; t++) {
+        Sb[(((t - 1) * V3_NW + warp) * 2 + 0) * 32 + lane] = N[t][0];
+        Sb[(((t - 1) * V3_NW + warp) * 2 + 1) * 32 + lane] = N[t][3];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        const f2 up = t == 0 ? rs[ru * 32 + lane] : Sb[(((t - 1) * V3_NW + wu) * 2 + 1) * 32 + lane];
+        const f2 dn = t == 0 ? rs[rd * 32 + lane] : Sb[(((t - 1) * V3_NW + wd) * 2 + 0) * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const f2 v = N[t][k];
+            const float lft = __shfl_up_sync(0xffffffffu, hi_of(v), 1);
+            const float rgt = __shfl_down_sync(0xffffffffu, lo_of(v), 1);
+            // left cell: (left lane's high) + own high; right cell: own low + (right lane's low)
+            const f2 xs = pk(__fadd_rn(lft, hi_of(v)), __fadd_rn(lo_of(v), rgt));
+            const f2 ys = add2(k == 0 ? up : N[t][k - 1], k == 3 ? dn : N[t][k + 1]);
+            Pp[t][k] = add2(add2(xs, ys), C[t][k]);
+        }
+    }
+}
+
+template <int T>
+constexpr size_t v4_smem_bytes() {
+    return sizeof(f2) * ((size_t)V4_RS * V3_H * 32 + 2 * (T > 1 ? T - 1 : 1) * V3_NW * 2 * 32);
+}
+
+}  // namespace
+
+template <int T>
+__global__ void __launch_bounds__(V3_NW * 32, 1)
+    k_heat3d_v4(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
+                float r) {
+    constexpr int BX = 64 - 2 * T, BY = V3_H - 2 * T;
+    extern __shared__ __align__(16) f2 v4_smem[];
+    f2 *ring = v4_smem;
+    f2 *sbase = v4_smem + (size_t)V4_RS * V3_H * 32;
+    constexpr int SB = (T > 1 ? T - 1 : 1) * V3_NW * 2 * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wu = warp > 0 ? warp - 1 : 0, wd = warp + 1 < V3_NW ? warp + 1 : V3_NW - 1;
+    const int ru = warp > 0 ? 4 * warp - 1 : 0, rd = warp + 1 < V3_NW ? 4 * warp + 4 : V3_H - 1;
+    const int tiles_x = (nx + BX - 1) / BX, tiles_y = (ny + BY - 1) / BY;
+    const int64_t work = (int64_t)tiles_x * tiles_y * nz;
+    const int64_t w_end = work * (blockIdx.x + 1) / gridDim.x;
+    const size_t plane = (size_t)ny * nx;
+    const f2 r2 = pk(r, r), m6 = pk(-6.0f, -6.0f);
+    int buf = 0;
+
+    for (int64_t w = work * blockIdx.x / gridDim.x; w < w_end;) {
+        const int64_t reg = w / nz;
+        const int za = (int)(w - reg * nz);
+        const int zb = (int)min((int64_t)nz, za + (w_end - w));
+        w += zb - za;
+        const int tx = (int)(reg % tiles_x), ty = (int)(reg / tiles_x);
+        const int x0 = tx * BX - T, y0 = ty * BY - T;
+        const int c0 = 2 * lane;
+        const unsigned gx0 = wrapi(x0 + c0, nx), gx1 = wrapi(x0 + c0 + 1, nx);
+        const bool pair = gx1 == gx0 + 1 && (gx0 & 1u) == 0 && (nx & 1) == 0;
+        const bool ox0 = c0 >= T && c0 < 64 - T && x0 + c0 < nx;
+        const bool ox1 = c0 + 1 >= T && c0 + 1 < 64 - T && x0 + c0 + 1 < nx;
+        unsigned row[4], omask = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int q = 4 * warp + k;
+            row[k] = (unsigned)wrapi(y0 + q, ny) * (unsigned)nx;
+            const bool oy = q >= T && q < V3_H - T && y0 + q < ny;
+            omask |= (oy && ox0 ? 1u : 0u) << (2 * k);
+            omask |= (oy && ox1 ? 2u : 0u) << (2 * k);
+        }
+
+        f2 X[T][4], Y[T][4], Pp[T][4];
+#pragma unroll
+        for (int t = 0; t < T; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) X[t][k] = Y[t][k] = Pp[t][k] = 0ull;
+        // iteration j receives level-0 plane za - T + j (ring slot j % V4_RS)
+        // and emits level-T plane za - 2T + j (stored for j >= 2T)
+        const int iters = (zb - za) + 2 * T;
+        int zf = wrapi(za - T, nz);
+        v4_fetch(ring, 0, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+#pragma unroll
+        for (int q = 1; q < V4_D; q++) {
+            zf = zf + 1 < nz ? zf + 1 : 0;
+            v4_fetch(ring, q, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+        }
+        int slot = 0;
+        for (int j = 0; j < iters; j += 2) {
+            int fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
+            v4_iter<T, 0>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
+                          zf, nz, plane, j >= 2 * T, za - 2 * T + j, omask, lane, warp, ru, rd, wu,
+                          wd, r2, m6);
+            buf ^= 1;
+            slot = slot + 1 < V4_RS ? slot + 1 : 0;
+            if (j + 1 >= iters) break;
+            fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
+            v4_iter<T, 1>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
+                          zf, nz, plane, j + 1 >= 2 * T, za - 2 * T + j + 1, omask, lane, warp, ru,
+                          rd, wu, wd, r2, m6);
+            buf ^= 1;
+            slot = slot + 1 < V4_RS ? slot + 1 : 0;
+        }
+        // the copies fetched past the segment land before the ring is reused
+        cp_wait<0>();
+        __syncthreads();
+    }
+}
+
+template <int T>
+cudaError_t v4_launch(unsigned g, const float *src, float *dst, int nz, int ny, int nx, float r,
+                      cudaStream_t s) {
+    constexpr size_t smem = v4_smem_bytes<T>();
+    static bool attr = false;  // idempotent, so a race between first callers is harmless
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_heat3d_v4<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_heat3d_v4<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r);
+    return cudaGetLastError();
+}
+
 int heat3d_blocks(int nz, int ny, int nx, int T, int zchunk) {
     const int BX = RX - 2 * T, BY = RY - 2 * T;
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + zchunk - 1) / zchunk);
@@ -674,12 +875,20 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
     unsigned g = cfg ? cfg->grid[0] * cfg->grid[1] * cfg->grid[2] : (unsigned)blocks;
     // variant 3 keeps in-plane offsets in 32 bits; larger planes take variant 2 (same bits)
     const int64_t variant = tune::get("heat3d.variant");
-    if (variant == 3 && (uint64_t)ny * (uint64_t)nx <= 0xffffffffull) {
+    if (variant >= 3 && (uint64_t)ny * (uint64_t)nx <= 0xffffffffull) {
         if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != V3_NW * 32)
             return cudaErrorInvalidValue;
         const int BX = 64 - 2 * steps, BY = V3_H - 2 * steps;
         const int64_t work = (int64_t)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
         const unsigned g3 = cfg ? g : (unsigned)std::min<int64_t>(sm_count(), work);
+        if (variant == 4) {
+            switch (steps) {
+                case 1: return v4_launch<1>(g3, src, dst, nz, ny, nx, r, s);
+                case 2: return v4_launch<2>(g3, src, dst, nz, ny, nx, r, s);
+                case 3: return v4_launch<3>(g3, src, dst, nz, ny, nx, r, s);
+                case 4: return v4_launch<4>(g3, src, dst, nz, ny, nx, r, s);
+            }
+        }
         switch (steps) {
             case 1: return v3_launch<1>(g3, src, dst, nz, ny, nx, r, s);
             case 2: return v3_launch<2>(g3, src, dst, nz, ny, nx, r, s);

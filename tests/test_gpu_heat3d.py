@@ -73,7 +73,7 @@ def test_heat3d_bitexact_across_blocking(dev):
 def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     """Every form of the 3D kernel (plane registers copied, rotated, rotated
     with paired FP32 instructions, two planes per level with the z range split
-    over the CTAs) and every z split give the bits of one plain step per launch
+    over the CTAs, the same with a cp.async plane ring) and every z split give the bits of one plain step per launch
     of the default form; odd nx takes the scalar-load path, small nz the
     wrapped z index."""
     u0 = synth.heat3d_input(shape[2], seed=330 + shape[0], nz=shape[0], ny=shape[1])
@@ -81,7 +81,7 @@ def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     want = oracle.heat3d(u0.astype(np.float64), float(R), 9)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.zchunks")}
     try:
-        for variant in (0, 1, 2, 3):
+        for variant in (0, 1, 2, 3, 4):
             hxc.tune_set("heat3d.variant", variant)
             for nch in (0, 1, 3):
                 hxc.tune_set("heat3d.zchunks", nch)
@@ -145,8 +145,8 @@ def test_heat3d_product_mode_full_size(dev):
 
 @pytest.mark.parametrize("shape", [(33, 200, 130), (5, 64, 64), (70, 57, 250)])
 def test_heat3d_two_plane_form_any_grid(dev, shape):
-    """The two-plane form (variant 3) splits the (region, plane) pairs evenly
-    over whatever grid it is launched with: one CTA, a few CTAs whose shares
+    """The two-plane forms (variants 3 and 4) split the (region, plane) pairs
+    evenly over whatever grid they are launched with: one CTA, a few CTAs whose shares
     span several regions, and more CTAs than pairs (empty shares) all give the
     bits of the copied-plane form (variant 0); 1..4 steps per launch."""
     u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=340 + shape[0], nz=shape[0],
@@ -156,7 +156,8 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
     try:
         for steps in (1, 2, 3, 4):
             want = None
-            for variant, grid in ((0, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000)):
+            for variant, grid in ((0, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000),
+                                  (4, None), (4, 1), (4, 7), (4, 100000)):
                 hxc.tune_set("heat3d.variant", variant)
                 a.write(u0).get()
                 args = hxc.hxc_heat3d_args(a.h, b.h, shape[0], shape[1], shape[2], R, steps)
