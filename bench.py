@@ -396,8 +396,14 @@ def secondary(dev, timer, peaks):
     # per-launch HBM roofline of the 4-step kernel (algorithmic: read + write once)
     launch_ms = res["fused"]["ms"] / (st3 / 4)
     gbs = 2 * u3.nbytes / (launch_ms / 1e3) / 1e9
+    traffic3 = None
+    tp3 = os.path.join(HERE, "profiles", "heat3d_traffic.json")
+    if os.path.exists(tp3):
+        traffic3 = json.load(open(tp3)).get("bytes_per_launch")
     res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": gbs / peaks["hbm_gbs"], "ms_per_launch": launch_ms,
+                       "traffic": traffic3,
+                       "kernel": "k_heat3d_v4<4> (4 steps of the whole 512^3 field per launch)",
                        "effective_gbs_1step_equiv": 2 * u3.nbytes * st3 / (res["fused"]["ms"] / 1e3) / 1e9}
     out["heat3d_512^3_200steps_f32"] = res
     del u3
