@@ -541,10 +541,11 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
 /* Launch-shape and work-split knobs of the built-in kernels (the
  * autotuner's parameters).  They change speed only: every value gives
  * bit-identical results.  Values are clamped to their ranges.  Keys:
- *   "heat2d.emul"  share of the 2D stencil's three FP64 additions computed by
- *                  the integer-pipe IEEE adder instead of the FP64 pipe, in
- *                  half-additions per point, 0..6 (default 0).
- *   "heat2d.rows"  rows each warp of the 2D kernel walks (default 8).
+ *   "heat2d.emul"  share of the 2D stencil's two FP64 additions per point
+ *                  (its pair sum and the sum of its two pair sums) computed
+ *                  by the integer-pipe IEEE adder instead of the FP64 pipe,
+ *                  in half-additions per point, 0..4 (default 0).
+ *   "heat2d.rows"  rows each warp of the 2D kernel walks (default 16).
  *   "heat2d.occupancy"  minimum resident 256-thread CTAs per SM the 2D
  *                  kernel is compiled for, 4..6 (default 4).
  *   "heat3d.zchunks"  z chunks of a 3D launch of forms 0..2, 0 = fill whole

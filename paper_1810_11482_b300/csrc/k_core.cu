@@ -6,9 +6,13 @@
 // same sequence of correctly rounded FP64 operations, so results are
 // bit-identical across partition counts, schedules and graph replay:
 //   1D: s = ul + ur;                 t = fma(-2, u, s); u' = fma(r, t, u)
-//   2D: s = (uW + uE) + (uN + uS);   t = fma(-4, u, s); u' = fma(r, t, u)
+//   2D: s = (uN + uW) + (uE + uS);   t = fma(-4, u, s); u' = fma(r, t, u)
 // (the additions are issued as fma(a, 1, b), which rounds identically).
-// The neighbour sums are symmetric, so mirrored inputs give mirrored bits.
+// The 2D neighbours are paired along the anti-diagonal: uE + uS of a point
+// is also uN + uW of the point below and to the right, so each pair sum is
+// computed once and used by two points (4 FP64 operations per point).  The
+// sums are symmetric under transposition and under a half turn, so
+// transposed or reversed inputs give transposed or reversed bits.
 #include "fp64_int.cuh"
 #include "kernels.cuh"
 #include "tune.hpp"
@@ -55,22 +59,20 @@ __device__ __forceinline__ double ftcs3(double ul, double u, double ur, double r
     return __fma_rn(r, t, u);
 }
 
-__device__ __forceinline__ double ftcs5(double u, double w, double e, double n, double so,
-                                        double r, double one) {
-    double s = addf(addf(w, e, one), addf(n, so, one), one);
-    double t = __fma_rn(-4.0, u, s);
-    return __fma_rn(r, t, u);
+// One 2D pair sum (uE + uS of a point, = uN + uW of the point below and to
+// the right), on the integer-pipe adder when E >= 1.
+template <int E>
+__device__ __forceinline__ double pair2(double a, double b, double one) {
+    return E >= 1 ? dadd_int(a, b) : addf(a, b, one);
 }
 
-// The same update with its first EM additions (EM = 0..3, in the order
-// w+e, n+s, outer sum) computed by the integer-pipe adder.  Every EM gives
-// the same bits; the split balances the FP64 pipe against the integer pipe.
-template <int EM>
-__device__ __forceinline__ double ftcs5e(double u, double w, double e, double n, double so,
-                                         double r, double one) {
-    const double h = EM >= 1 ? dadd_int(w, e) : addf(w, e, one);
-    const double v = EM >= 2 ? dadd_int(n, so) : addf(n, so, one);
-    const double s = EM >= 3 ? dadd_int(h, v) : addf(h, v, one);
+// The 2D update from the point's two pair sums, pNW = uN + uW and
+// pSE = uE + uS; their sum on the integer-pipe adder when E >= 2.  Every E
+// gives the same bits; the split balances the FP64 pipe against the
+// integer pipe.
+template <int E>
+__device__ __forceinline__ double ftcs5p(double u, double pNW, double pSE, double r, double one) {
+    const double s = E >= 2 ? dadd_int(pNW, pSE) : addf(pNW, pSE, one);
     const double t = __fma_rn(-4.0, u, s);
     return __fma_rn(r, t, u);
 }
@@ -203,9 +205,16 @@ cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_
 
 // ------------------------------------------------------------ 2D FTCS
 // A warp owns a strip of 32*V columns (V consecutive columns per lane) and
-// `H` rows, walks the rows keeping rows y-1, y, y+1 in registers, and gets
-// its x-neighbours from the adjacent lanes by shuffles; the two columns just
-// outside the strip are read from global memory (zero outside the field).
+// `H` rows and walks the rows keeping rows y and y+1 in registers.  Walking
+// row y it forms the pair sums P(y, x) = u[y][x+1] + u[y+1][x] of its
+// columns (the right neighbour of its last column from the next lane by a
+// shuffle, or from memory at the strip's right end) and updates row y with
+// S(y, x) = P(y-1, x-1) + P(y, x): P(y-1, x-1) is the previous row's pair
+// sum of the column to the left (own register, or the left lane's by a
+// shuffle).  Lane 0's P(y-1, xs-1) straddles the strip's left edge; those
+// are formed for 32 rows at a time, one row per lane, and handed to lane 0
+// by a shuffle.  The row above the strip seeds P(ys-1, .).  Values outside
+// the field are zero.
 template <int V>
 struct Vec;
 template <>
@@ -256,40 +265,58 @@ __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__
         const int64_t xl = xs + (int64_t)lane * V;
         const bool active = xl < xe;
         const bool last = active && xl + V >= xe;  // owns the strip's last column
-        Vec<V> prv, cur, nxt;
-        load_row<V>(prv, src, ny, nx, ys - 1, xl, active);
-        load_row<V>(cur, src, ny, nx, ys, xl, active);
-        // the strip's outside neighbours (lane 0's left, the last lane's
-        // right), loaded one row ahead like the rows themselves
-        double eL = lane == 0 ? at2(src, ny, nx, ys, xs - 1) : 0.0;
-        double eR = last ? at2(src, ny, nx, ys, xl + V) : 0.0;
-        for (int64_t y = ys; y < ye; y++) {
-            load_row<V>(nxt, src, ny, nx, y + 1, xl, active);
-            const double eLn = lane == 0 && y + 1 < ye ? at2(src, ny, nx, y + 1, xs - 1) : 0.0;
-            const double eRn = last && y + 1 < ye ? at2(src, ny, nx, y + 1, xl + V) : 0.0;
-            double hi;
-            if constexpr (V == 2)
-                hi = cur.b;
-            else
-                hi = cur.a;
-            double left = __shfl_up_sync(0xffffffffu, hi, 1);
-            double right = __shfl_down_sync(0xffffffffu, cur.a, 1);
-            if (lane == 0) left = eL;
-            if (last) right = eR;
-            eL = eLn;
-            eR = eRn;
-            if (active) {
-                if constexpr (V == 2) {
-                    double2 o;
-                    o.x = ftcs5e<EA>(cur.a, left, cur.b, prv.a, nxt.a, r, one);
-                    o.y = ftcs5e<EB>(cur.b, cur.a, right, prv.b, nxt.b, r, one);
-                    *reinterpret_cast<double2 *>(dst + y * nx + xl) = o;
-                } else {
-                    dst[y * nx + xl] = ftcs5e<EA>(cur.a, left, right, prv.a, nxt.a, r, one);
-                }
+        Vec<V> cur, nxt;
+        // pair sums of row ys-1: P(ys-1, x) = u[ys-1][x+1] + u[ys][x]
+        double pp0, pp1 = 0.0;  // P(y-1, xl), P(y-1, xl+1)
+        {
+            Vec<V> prv;
+            load_row<V>(prv, src, ny, nx, ys - 1, xl, active);
+            load_row<V>(cur, src, ny, nx, ys, xl, active);
+            double rgt = __shfl_down_sync(0xffffffffu, prv.a, 1);
+            if (last) rgt = at2(src, ny, nx, ys - 1, xl + V);
+            if constexpr (V == 2) {
+                pp0 = pair2<EA>(prv.b, cur.a, one);
+                pp1 = pair2<EB>(rgt, cur.b, one);
+            } else {
+                pp0 = pair2<EA>(rgt, cur.a, one);
             }
-            prv = cur;
-            cur = nxt;
+        }
+        // right neighbour of the strip's last column, one row ahead
+        double eR = last ? at2(src, ny, nx, ys, xl + V) : 0.0;
+        for (int64_t yb = ys; yb < ye; yb += 32) {
+            const int64_t yn = min(ye, yb + 32);
+            // lane k: P(yb+k-1, xs-1) = u[yb+k-1][xs] + u[yb+k][xs-1]
+            double pe = 0.0;
+            if (yb + lane < yn)
+                pe = pair2<EA>(at2(src, ny, nx, yb + lane - 1, xs), at2(src, ny, nx, yb + lane, xs - 1),
+                               one);
+            for (int64_t y = yb; y < yn; y++) {
+                load_row<V>(nxt, src, ny, nx, y + 1, xl, active);
+                const double eRn = last && y + 1 < ye ? at2(src, ny, nx, y + 1, xl + V) : 0.0;
+                double rgt = __shfl_down_sync(0xffffffffu, cur.a, 1);
+                if (last) rgt = eR;
+                double pnw = __shfl_up_sync(0xffffffffu, V == 2 ? pp1 : pp0, 1);
+                const double pel = __shfl_sync(0xffffffffu, pe, (int)(y - yb));
+                if (lane == 0) pnw = pel;
+                if constexpr (V == 2) {
+                    const double q0 = pair2<EA>(cur.b, nxt.a, one);
+                    const double q1 = pair2<EB>(rgt, nxt.b, one);
+                    if (active) {
+                        double2 o;
+                        o.x = ftcs5p<EA>(cur.a, pnw, q0, r, one);
+                        o.y = ftcs5p<EB>(cur.b, pp0, q1, r, one);
+                        *reinterpret_cast<double2 *>(dst + y * nx + xl) = o;
+                    }
+                    pp0 = q0;
+                    pp1 = q1;
+                } else {
+                    const double q0 = pair2<EA>(rgt, nxt.a, one);
+                    if (active) dst[y * nx + xl] = ftcs5p<EA>(cur.a, pnw, q0, r, one);
+                    pp0 = q0;
+                }
+                eR = eRn;
+                cur = nxt;
+            }
         }
     }
 }
@@ -315,7 +342,7 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
     unsigned b = block_from(cfg, 256);
     unsigned g = grid_from(cfg, std::min<int64_t>((nwork + b / 32 - 1) / (b / 32), (int64_t)sm_count() * 64));
     // integer-pipe share of the additions, in half-additions per point
-    // (0..6: points a and b of a lane take floor/ceil of half of it), and
+    // (0..4: points a and b of a lane take floor/ceil of half of it), and
     // the minimum resident CTAs per SM the kernel is compiled for (4..6)
     const int em = heat2d_emul(), occ = heat2d_occupancy();
 #define HXC_L2D(VV, A, B, M) k_heat2d<VV, A, B, M><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0)
@@ -323,8 +350,7 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
         switch (em / 2) {
             case 0: HXC_L2D(1, 0, 0, 4); break;
             case 1: HXC_L2D(1, 1, 1, 4); break;
-            case 2: HXC_L2D(1, 2, 2, 4); break;
-            default: HXC_L2D(1, 3, 3, 4); break;
+            default: HXC_L2D(1, 2, 2, 4); break;
         }
         return cudaGetLastError();
     }
@@ -340,9 +366,7 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
         case 1: HXC_L2D(2, 0, 1, 4); break;
         case 2: HXC_L2D(2, 1, 1, 4); break;
         case 3: HXC_L2D(2, 1, 2, 4); break;
-        case 4: HXC_L2D(2, 2, 2, 4); break;
-        case 5: HXC_L2D(2, 2, 3, 4); break;
-        default: HXC_L2D(2, 3, 3, 4); break;
+        default: HXC_L2D(2, 2, 2, 4); break;
     }
 #undef HXC_L2D
     return cudaGetLastError();

@@ -25,8 +25,8 @@ struct Knob {
 
 // key, default, min, max
 Knob g_knobs[] = {
-    {"heat2d.emul", 0, 0, 6},         // integer-pipe share of the 2D additions
-    {"heat2d.rows", 8, 1, 4096},      // rows per warp of the 2D kernel
+    {"heat2d.emul", 0, 0, 4},         // integer-pipe share of the 2D additions
+    {"heat2d.rows", 16, 1, 4096},     // rows per warp of the 2D kernel
     {"heat2d.occupancy", 4, 4, 6},    // compiled minimum of CTAs per SM
     {"heat3d.zchunks", 0, 0, 64},     // z chunks per launch (0: fill whole waves)
     {"heat3d.variant", 4, 0, 4},      // 0 copied, 1 rotated, 2 rotated + f32x2, 3 two-plane, 4 + ring

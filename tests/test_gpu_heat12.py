@@ -186,9 +186,13 @@ def test_heat2d_bitexact_across_tilings_and_modes(dev):
         for mode in ("plain", "graph", "fused"):
             got, _, _, _ = run2d(dev, u0, tiles, 0.2, 25, mode)
             assert np.array_equal(got, ref), (tiles, mode)
-    # mirror symmetry is exact: the flipped input gives the flipped output
+    # the pair sums (uN + uW) + (uE + uS) are symmetric under a half turn and
+    # under transposition: the turned or transposed input gives the turned or
+    # transposed output bit for bit
     got, _, _, _ = run2d(dev, u0[::-1, ::-1].copy(), (2, 2), 0.2, 25, "fused")
     assert np.array_equal(got, ref[::-1, ::-1])
+    got, _, _, _ = run2d(dev, u0.T.copy(), (3, 2), 0.2, 25, "fused")
+    assert np.array_equal(got, ref.T)
 
 
 def test_heat2d_snapshot_norms(dev):
@@ -303,15 +307,15 @@ def test_heat2d_integer_adder_splits_are_bit_identical(dev):
                   synth.uniform(241, 97 * 131, lo=-1, hi=1).reshape(97, 131)]
         for u0 in fields:
             outs = []
-            for em in range(7):
+            for em in range(5):
                 hxc.tune_set("heat2d.emul", em)
                 got, _, _, _ = run2d(dev, u0, (2, 3), 0.2, 7, "fused")
                 outs.append(got)
-            for em in range(1, 7):
+            for em in range(1, 5):
                 assert np.array_equal(outs[em].view(np.uint64), outs[0].view(np.uint64)), em
         want = oracle.heat2d(fields[0], 0.2, 7)
         assert relerr(outs[0], oracle.heat2d(fields[2], 0.2, 7)) <= TOL
-        hxc.tune_set("heat2d.emul", 6)
+        hxc.tune_set("heat2d.emul", 4)
         got, _, _, _ = run2d(dev, fields[0], (2, 3), 0.2, 7, "plain")
         assert relerr(got, want) <= TOL
     finally:
@@ -324,7 +328,7 @@ def test_heat2d_integer_adder_full_size(dev):
         u0 = synth.bumps2d(8192, 8192, seed=2)
         hxc.tune_set("heat2d.emul", 0)
         a, _, _, _ = run2d(dev, u0, (8, 8), 0.2, 1000, "fused")
-        for em in (3, 5):
+        for em in (3, 4):
             hxc.tune_set("heat2d.emul", em)
             b, _, _, _ = run2d(dev, u0, (8, 8), 0.2, 1000, "fused")
             assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), em
