@@ -32,7 +32,7 @@ class _Timer:
         for e in self.ev:
             assert self.rt.cudaEventCreate(ctypes.byref(e)) == 0
 
-    def time(self, issue, reps=2):
+    def time(self, issue, reps=3):
         """Best time in ms of issue(deps) -> Future, after one warm-up."""
         issue(()).get()
         best = float("inf")
@@ -86,7 +86,7 @@ def tune(quick=False, log=print):
     u0 = synth.bumps2d(n, n, seed=2)
     u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
     u.write(u0).get()
-    cfg = hxc.heat2d_cfg(n, n, 1, 1, 0.2, 40, 0, "fused", None, None)
+    cfg = hxc.heat2d_cfg(n, n, 1, 1, 0.2, 100, 0, "fused", None, None)
     log("heat2d")
     result.update(_search(timer, {"heat2d.occupancy": [4, 5, 6], "heat2d.rows": [8, 16, 32, 64]},
                           lambda d: hxc.heat2d_run(dev, u, t, cfg, d)[0], log))
@@ -97,9 +97,14 @@ def tune(quick=False, log=print):
     a, b = dev.buffer(u3.nbytes), dev.buffer(u3.nbytes)
     a.write(u3).get()
     log("heat3d")
-    result.update(_search(timer, {"heat3d.variant": [0, 1, 2, 3, 4], "heat3d.zchunks": [0, 1, 2, 3, 4, 6, 8]},
-                          lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 8, "fused", 4, d)[0],
-                          log))
+    run3 = lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 8, "fused", 4, d)[0]
+    hxc.tune_set("heat3d.zchunks", 0)
+    best3 = _search(timer, {"heat3d.variant": [0, 1, 2, 3, 4]}, run3, log)
+    # the z split applies to the forms that cut z into chunks (0..2); forms 3
+    # and 4 split the (region, plane) pairs evenly over the SMs themselves
+    if best3["heat3d.variant"] <= 2:
+        best3.update(_search(timer, {"heat3d.zchunks": [0, 1, 2, 3, 4, 6, 8]}, run3, log))
+    result.update(best3)
     del a, b
     # 1D: CTAs per partition of the temporally blocked kernel
     n1 = 1 << 20
