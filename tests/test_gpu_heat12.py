@@ -195,6 +195,29 @@ def test_heat2d_bitexact_across_tilings_and_modes(dev):
     assert np.array_equal(got, ref.T)
 
 
+def test_heat2d_rows_and_occupancy_knobs_bitexact(dev):
+    """The strip height (rows per warp, including heights that are not
+    multiples of the 32-row groups in which the strip-edge pair sums are
+    formed) and the compiled occupancy change speed only: every value gives
+    the bits of the default, on an even width (two columns per lane) and an
+    odd width (one column per lane), tiled and whole-field."""
+    old = {k: hxc.tune_get(k) for k in ("heat2d.rows", "heat2d.occupancy")}
+    try:
+        for u0, tiles in ((synth.bumps2d(300, 386, seed=230, nbumps=6, sigma=0.05), (3, 2)),
+                          (synth.uniform(231, 97 * 131, lo=-1, hi=1).reshape(97, 131), (1, 1))):
+            ref, _, _, _ = run2d(dev, u0, tiles, 0.2, 9, "fused")
+            assert relerr(ref, oracle.heat2d(u0, 0.2, 9)) <= TOL
+            for rows in (1, 3, 16, 31, 32, 33, 64, 100, 4096):
+                for occ in (4, 6):
+                    hxc.tune_set("heat2d.rows", rows)
+                    hxc.tune_set("heat2d.occupancy", occ)
+                    got, _, _, _ = run2d(dev, u0, tiles, 0.2, 9, "fused")
+                    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), (rows, occ)
+    finally:
+        for k, v in old.items():
+            hxc.tune_set(k, v)
+
+
 def test_heat2d_snapshot_norms(dev):
     """Host norms (then-continuations on device->host snapshots) and device
     norms (fixed-order reduction) against the oracle's tile norms."""
