@@ -115,6 +115,22 @@ def test_heat1d_bitexact_across_schedules(dev):
             assert np.array_equal(got, ref), (parts, mode, spl)
 
 
+def test_heat1d_translation_and_reflection_exact(dev):
+    """Periodic boundaries and a sum uL + uR that is symmetric: a circular
+    shift of the input (across partition boundaries and the wrap) gives the
+    same shift of the output, and the reversed input the reversed output,
+    bit for bit, in every mode."""
+    n, steps, r = 4099, 23, 0.25
+    u0 = synth.uniform(102, n, lo=-1, hi=1)
+    ref, _ = run1d(dev, u0, 5, r, steps, "fused")
+    for k in (1, 37, n // 2, n - 3):
+        for mode in ("plain", "fused"):
+            got, _ = run1d(dev, np.roll(u0, k), 5, r, steps, mode)
+            assert np.array_equal(got, np.roll(ref, k)), (k, mode)
+    got, _ = run1d(dev, u0[::-1].copy(), 3, r, steps, "graph")
+    assert np.array_equal(got, ref[::-1])
+
+
 def test_heat1d_full_config_vs_oracle(dev):
     """2^20 points, 8 partitions, r = 1/4, 100 steps, every mode."""
     n, r, steps = 1 << 20, 0.25, 100

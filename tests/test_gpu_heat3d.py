@@ -69,6 +69,30 @@ def test_heat3d_bitexact_across_blocking(dev):
     assert np.array_equal(a, np.swapaxes(b, 1, 2))
 
 
+def test_heat3d_translation_and_reflection_exact(dev):
+    """Periodic boundaries: a circular shift of the input along z, y and x
+    (moving the data across region edges, the wrap and the z splits) gives
+    the same shift of the output bit for bit, for every kernel form; the x and
+    y pairs are symmetric sums, so reversing x or y reverses the output."""
+    shape = (37, 150, 200)
+    u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=350, nz=shape[0], ny=shape[1]),
+                              dtype=np.float32)
+    old = hxc.tune_get("heat3d.variant")
+    try:
+        for variant in (2, 3, 4):
+            hxc.tune_set("heat3d.variant", variant)
+            ref, _ = run3d(dev, u0, 8, "fused", 4)
+            for sh in ((5, 0, 0), (0, 61, 0), (0, 0, 77), (19, 100, 3)):
+                got, _ = run3d(dev, np.roll(u0, sh, axis=(0, 1, 2)), 8, "fused", 4)
+                assert np.array_equal(got, np.roll(ref, sh, axis=(0, 1, 2))), (variant, sh)
+            got, _ = run3d(dev, u0[:, ::-1, :].copy(), 8, "fused", 4)
+            assert np.array_equal(got, ref[:, ::-1, :]), variant
+            got, _ = run3d(dev, u0[:, :, ::-1].copy(), 8, "fused", 4)
+            assert np.array_equal(got, ref[:, :, ::-1]), variant
+    finally:
+        hxc.tune_set("heat3d.variant", old)
+
+
 @pytest.mark.parametrize("shape", [(40, 72, 96), (9, 70, 131), (8, 8, 8), (21, 33, 64)])
 def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     """Every form of the 3D kernel (plane registers copied, rotated, rotated
