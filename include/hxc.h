@@ -211,13 +211,17 @@ typedef enum {
     /* 1D FTCS: dst[lo, lo+count) = `steps` periodic steps of src.  steps > 1
      * reads a halo of width `steps` from src (temporal blocking). */
     HXC_K_HEAT1D = 3,
-    /* 2D FTCS step on the tile [y0, y0+ty) x [x0, x0+tx). */
+    /* 2D FTCS step on the tile [y0, y0+ty) x [x0, x0+tx), zero outside the
+     * field; every point rounds t = fma(-4, u, (uN + uW) + (uE + uS)),
+     * u' = fma(r, t, u) in FP64, so any tiling gives the same bits. */
     HXC_K_HEAT2D = 4,
     /* Tile snapshot and squared norm: copies the tile of src into the compact
      * ty x tx buffer snap (optional) and stores sum(u^2) of the tile in
      * sums[sum_index] with a fixed reduction order. */
     HXC_K_TILE_NORM2 = 5,
-    /* 3D FTCS, FP32, `steps` (1..4) fused steps per launch. */
+    /* 3D FTCS, FP32, periodic, `steps` (1..4) fused steps per launch; every
+     * cell rounds t = fma(-6, u, (((x- + x+) + (y- + y+)) + z-) + z+),
+     * u' = fma(r, t, u) in FP32, so any blocking gives the same bits. */
     HXC_K_HEAT3D = 6,
     /* Variable-diffusivity FTCS step (flux form, arithmetic face mean). */
     HXC_K_VARCOEF2D = 7,
