@@ -195,6 +195,20 @@ def test_heat2d_vs_oracle_small(dev, shape, tiles):
                 assert relerr(got, want) <= TOL, (mode, r, steps)
 
 
+@pytest.mark.parametrize("shape,tiles", [((1, 1), (1, 1)), ((1, 7), (1, 3)), ((7, 1), (3, 1)),
+                                         ((2, 3), (2, 1)), ((3, 64), (1, 2)), ((65, 2), (5, 1)),
+                                         ((5, 130), (5, 2)), ((129, 3), (2, 3))])
+def test_heat2d_degenerate_shapes(dev, shape, tiles):
+    """Single rows and columns, fields narrower than a lane's two columns,
+    widths just past a strip, one-row tiles: every mode against the oracle."""
+    u0 = synth.uniform(250 + shape[0] * 7 + shape[1], shape[0] * shape[1], lo=-1, hi=1).reshape(shape)
+    for steps in (1, 4):
+        want = oracle.heat2d(u0, 0.2, steps)
+        for mode in ("plain", "graph", "fused"):
+            got, _, _, _ = run2d(dev, u0, tiles, 0.2, steps, mode)
+            assert np.max(np.abs(got - want)) <= 1e-15, (mode, steps)
+
+
 def test_heat2d_bitexact_across_tilings_and_modes(dev):
     u0 = synth.bumps2d(512, 384, seed=210, nbumps=8, sigma=0.05)
     ref, _, _, _ = run2d(dev, u0, (1, 1), 0.2, 25, "plain")

@@ -44,7 +44,8 @@ def relerr(a, b, scale=None):
     return float(np.max(np.abs(a.astype(np.float64) - b)) / scale)
 
 
-@pytest.mark.parametrize("shape", [(16, 24, 40), (9, 70, 130), (33, 31, 17), (8, 8, 8)])
+@pytest.mark.parametrize("shape", [(16, 24, 40), (9, 70, 130), (33, 31, 17), (8, 8, 8),
+                                   (1, 1, 1), (1, 2, 3), (2, 1, 5), (3, 65, 1), (1, 57, 129)])
 def test_heat3d_vs_oracle_small(dev, shape):
     u0 = synth.heat3d_input(shape[2], seed=300 + shape[0], nz=shape[0], ny=shape[1])
     for steps in (1, 3, 4, 9):
