@@ -191,6 +191,18 @@ hxc_status hxc_make_ready_future(hxc_status status, hxc_future *out);
 /* A future completed later by hxc_promise_set (host-side producer). */
 hxc_status hxc_promise_create(hxc_future *out);
 hxc_status hxc_promise_set(hxc_future promise, hxc_status status);
+
+/* Host-side fault injection for testing failure handling (the paper's
+ * futures carry errors, Sec. 3.1; it has no injection facility): after
+ * `after_ops` further device operations (copies, kernel launches, joins;
+ * 0 = the next one), one operation is not enqueued and its future completes
+ * with `status` (not HXC_OK), exactly as if its CUDA call had returned an
+ * error; operations that depend on it complete with HXC_E_DEP_FAILED and
+ * their continuations do not run.  Nothing faults on the device and the
+ * device stays usable.  Inside a graph capture the capture fails.  Process-
+ * wide and one-shot; after_ops < 0 disarms.  Returns HXC_E_INVALID for
+ * status == HXC_OK with after_ops >= 0. */
+hxc_status hxc_debug_inject(int64_t after_ops, hxc_status status);
 /* Interop with foreign CUDA streams (e.g. torch's current stream):
  * a future for everything issued so far on `stream` ... */
 hxc_status hxc_future_from_stream(hxc_device dev, void *stream, hxc_future *out);

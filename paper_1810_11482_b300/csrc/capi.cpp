@@ -514,6 +514,15 @@ hxc_status hxc_promise_set(hxc_future ph, hxc_status status) {
     return HXC_OK;
 }
 
+hxc_status hxc_debug_inject(int64_t after_ops, hxc_status status) {
+    if (after_ops >= 0 && status == HXC_OK) {
+        set_error("hxc_debug_inject: an injected failure needs a non-OK status");
+        return HXC_E_INVALID;
+    }
+    inject_arm(after_ops, status);
+    return HXC_OK;
+}
+
 hxc_status hxc_future_from_stream(hxc_device dh, void *stream, hxc_future *out) {
     CHECK_OUT(out);
     Ref<Device> d = dev_from_handle(dh);

@@ -638,10 +638,13 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
     // without snapshots the steps are issued (and captured) in intervals of
     // at most 100 steps, which bounds the size of a captured graph
     const int64_t every = want_snaps ? cfg->snapshot_every : std::min<int64_t>(cfg->steps, 100);
+    // the earlier runs' readers of the rings order this run's writes into them
+    // but must not pass on their own failures: an unrelated later run would
+    // otherwise fail with HXC_E_DEP_FAILED after one failed run
     std::vector<FutRef> ring_free[2], host_free[2];  // per ring slot, per tile
     for (int r2 = 0; r2 < 2; r2++) {
-        ring_free[r2] = carry.d2h[r2];
-        host_free[r2] = carry.conts[r2];
+        for (auto &f : carry.d2h[r2]) ring_free[r2].push_back(fut_order_only(f));
+        for (auto &f : carry.conts[r2]) host_free[r2].push_back(fut_order_only(f));
     }
     std::vector<FutRef> host_conts;
     std::vector<FutRef> finals;

@@ -480,6 +480,17 @@ struct PendingOp {
 
 void issue_now(PendingOp &p);
 
+std::atomic<int64_t> g_inject_left{-1};
+std::atomic<int> g_inject_status{HXC_E_CUDA};
+
+// True for exactly one operation: the one the armed countdown reaches.
+bool inject_fires() {
+    int64_t v = g_inject_left.load(std::memory_order_relaxed);
+    while (v >= 0)
+        if (g_inject_left.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+
 void issue_deferred(std::shared_ptr<PendingOp> p) {
     std::vector<std::pair<cudaEvent_t, int>> waits;
     DepCheck c = check_deps(p->dev.get(), p->deps, false, &waits);
@@ -539,6 +550,15 @@ void issue_now(PendingOp &p) {
         e = cudaStreamWaitEvent(s, w.first, 0);
         if (e != cudaSuccess) break;
     }
+    if (e == cudaSuccess && inject_fires()) {
+        set_error("injected failure of a device operation");
+        if (capturing) {
+            std::lock_guard<std::mutex> g(dev->m);
+            dev->cap_failed = true;
+        }
+        fut_set_done(p.out, (hxc_status)g_inject_status.load());
+        return;
+    }
     if (e == cudaSuccess && p.op) e = p.op(s);
     if (e != cudaSuccess) {
         hxc_status es = cuda_status(e, "enqueue");
@@ -572,6 +592,23 @@ void issue_now(PendingOp &p) {
     fut_set_issued(p.out, dev, ev, p.slot, capturing);
 }
 }  // namespace
+
+FutRef fut_order_only(const FutRef &f) {
+    if (!f) return f;
+    {
+        std::lock_guard<std::mutex> g(f->m);
+        if (f->state == Future::DONE) return FutRef();
+        if (f->state == Future::ISSUED) return f;
+    }
+    FutRef p = make_pending();
+    fut_on_done(f, [p](hxc_status) { fut_set_done(p, HXC_OK); });
+    return p;
+}
+
+void inject_arm(int64_t after, hxc_status status) {
+    g_inject_status.store((int)status);
+    g_inject_left.store(after < 0 ? -1 : after);
+}
 
 hxc_status issue_device_op(Device *dev, int slot, const std::vector<FutRef> &deps, StreamOp op,
                            std::vector<AnyRef> keep, FutRef *out) {

@@ -168,6 +168,12 @@ hxc_status fut_poll(const FutRef &f, int *ready);
 hxc_status fut_wait(const FutRef &f, int64_t timeout_ns);
 // Calls cb(status) once f is done (inline if it already is).
 void fut_on_done(const FutRef &f, std::function<void(hxc_status)> cb);
+// A dependency on f that orders without passing on f's failure: null when
+// f is final (nothing left to wait for), f itself when it is an issued
+// device operation (its event orders; an issued operation does not fail
+// afterwards short of a lost context), else a host future that completes
+// with HXC_OK once f is final.
+FutRef fut_order_only(const FutRef &f);
 
 // Checks a C handle and returns a new reference (null on error, with the
 // thread-local error set).
@@ -187,6 +193,11 @@ using StreamOp = std::function<cudaError_t(cudaStream_t s)>;
 hxc_status issue_device_op(Device *dev, int slot, const std::vector<FutRef> &deps, StreamOp op,
                            std::vector<AnyRef> keep, FutRef *out);
 hxc_status deps_from_handles(const hxc_future *deps, int ndeps, std::vector<FutRef> *v);
+
+// Host-side fault injection: the device operation that reaches issue after
+// `after` further ones (0: the next) is not enqueued and completes with
+// `status`, as if its CUDA call had failed.  after < 0 disarms.
+void inject_arm(int64_t after, hxc_status status);
 
 // ------------------------------------------------------------------- graph
 struct Graph : RefCounted {

@@ -177,6 +177,7 @@ _SIGS = {
     "hxc_make_ready_future": (c_st, [c_st, ctypes.POINTER(c_fut)]),
     "hxc_promise_create": (c_st, [ctypes.POINTER(c_fut)]),
     "hxc_promise_set": (c_st, [c_fut, c_st]),
+    "hxc_debug_inject": (c_st, [i64, c_st]),
     "hxc_future_from_stream": (c_st, [c_dev, ctypes.c_void_p, ctypes.POINTER(c_fut)]),
     "hxc_future_stream_wait": (c_st, [c_fut, ctypes.c_void_p]),
     "hxc_future_retain": (c_st, [c_fut]),
@@ -357,6 +358,13 @@ def promise():
 
 def promise_set(f, status=HXC_OK):
     check(lib().hxc_promise_set(f.h, status), "promise_set")
+
+
+def debug_inject(after_ops, status=None):
+    """Arms the host-side fault injection (hxc_debug_inject); after_ops < 0
+    disarms."""
+    check(lib().hxc_debug_inject(after_ops, HXC_E_CUDA if status is None else status),
+          "debug_inject")
 
 
 class Device:

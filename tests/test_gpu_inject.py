@@ -1,0 +1,282 @@
+"""Failure handling of the future layer with host-side fault injection
+(hxc_debug_inject): one device operation is made to fail at issue, as if its
+CUDA call had returned an error, without any fault on the device.  The
+failure must reach the run's future, operations and continuations that
+depend on it must not run, no wait may hang (every wait here is bounded),
+and the device must stay usable: the same run afterwards matches the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_11482_b300 import hxc, synth
+
+pytestmark = pytest.mark.gpu
+WAIT_NS = 60 * 10**9  # bounded waits: a hang fails the test instead of stalling it
+
+
+@pytest.fixture(scope="module")
+def dev():
+    devs = hxc.get_all_devices(2, 0)
+    assert devs
+    yield devs[0]
+    hxc.debug_inject(-1)
+
+
+def run2d(dev, u0, mode, tiles=(2, 3), steps=12, every=4, inject=None):
+    """A 2D run with snapshots and host norms; `inject` arms the injection
+    (counted from the run's first device operation) after the upload."""
+    ny, nx = u0.shape
+    u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    u.write(u0).get()
+    if inject is not None:
+        hxc.debug_inject(inject)
+    T = tiles[0] * tiles[1]
+    hn = np.zeros(steps // every * T)
+    cfg = hxc.heat2d_cfg(ny, nx, tiles[0], tiles[1], 0.2, steps, every, mode, hn, None)
+    f, _ = hxc.heat2d_run(dev, u, t, cfg)
+    return f, u
+
+
+def test_injected_failure_reaches_the_run_and_spares_the_device(dev):
+    u0 = synth.bumps2d(96, 130, seed=260, nbumps=4, sigma=0.1)
+    want = oracle.heat2d(u0, 0.2, 12)
+    for after in (0, 5, 37):
+        f, _ = run2d(dev, u0, "plain", inject=after)
+        st = f.wait(WAIT_NS)
+        assert st in (hxc.HXC_E_CUDA, hxc.HXC_E_DEP_FAILED), (after, st)
+        hxc.debug_inject(-1)
+        dev.synchronize()
+        f, u = run2d(dev, u0, "plain")
+        assert f.wait(WAIT_NS) == hxc.HXC_OK
+        got = np.empty_like(u0)
+        u.read_sync(got)
+        assert np.max(np.abs(got - want)) / np.max(np.abs(want)) <= 1e-12
+
+
+def test_dependants_and_continuations_of_a_failed_copy_do_not_run(dev):
+    n = 4096
+    x = np.arange(n, dtype=np.float64)
+    a = dev.buffer(n * 8)
+    a.write(np.zeros(n)).get()
+    ran = []
+    hxc.debug_inject(0, hxc.HXC_E_NOMEM)
+    w = a.write(x)  # the next device operation: fails with the injected status
+    assert w.wait(WAIT_NS) == hxc.HXC_E_NOMEM
+    args = hxc.hxc_partition_args(a.h, n, 0)
+    k = dev.launch(hxc.HXC_K_PARTITION, args, deps=[w])
+    assert k.wait(WAIT_NS) == hxc.HXC_E_DEP_FAILED
+    c = k.then(lambda: ran.append(1))
+    assert c.wait(WAIT_NS) == hxc.HXC_E_DEP_FAILED
+    j = hxc.when_all([k, dev.buffer(8).write(np.zeros(1))])
+    assert j.wait(WAIT_NS) == hxc.HXC_E_DEP_FAILED
+    assert ran == []
+    # the buffer still holds what was there before the failed write
+    out = np.empty(n)
+    a.read_sync(out)
+    assert np.array_equal(out, np.zeros(n))
+
+
+def test_injected_failure_inside_a_graph_capture(dev):
+    """A failure while a run captures its graph fails the run synchronously or
+    through its future; no broken graph is cached: the next run in graph mode
+    replays a fresh capture and matches the plain run bit for bit."""
+    u0 = synth.bumps2d(80, 64, seed=261, nbumps=3, sigma=0.1)
+    try:
+        f, _ = run2d(dev, u0, "graph", tiles=(2, 2), steps=10, every=5, inject=3)
+        assert f.wait(WAIT_NS) != hxc.HXC_OK
+    except hxc.HxcError:
+        pass
+    hxc.debug_inject(-1)
+    dev.synchronize()
+    f, u = run2d(dev, u0, "graph", tiles=(2, 2), steps=10, every=5)
+    assert f.wait(WAIT_NS) == hxc.HXC_OK
+    g = np.empty_like(u0)
+    u.read_sync(g)
+    f, u = run2d(dev, u0, "plain", tiles=(2, 2), steps=10, every=5)
+    assert f.wait(WAIT_NS) == hxc.HXC_OK
+    p = np.empty_like(u0)
+    u.read_sync(p)
+    assert np.array_equal(g, p)
+
+
+def test_injection_argument_checks(dev):
+    L = hxc.lib()
+    assert L.hxc_debug_inject(ctypes.c_int64(0), hxc.HXC_OK) == hxc.HXC_E_INVALID
+    assert L.hxc_debug_inject(ctypes.c_int64(-1), hxc.HXC_OK) == hxc.HXC_OK
+    # disarmed: the next operations run normally
+    b = dev.buffer(64)
+    b.write(np.ones(8)).get()
+
+
+# ------------------------------------------- every run entry point
+
+def _case_heat1d(dev, mode):
+    n = 5003
+    u0 = synth.heat1d_input(n, seed=270)
+    u, t = dev.buffer(n * 8), dev.buffer(n * 8)
+
+    def prepare():
+        u.write(u0).get()
+
+    def issue():
+        return hxc.heat1d_run(dev, u, t, n, 4, 0.25, 20, mode)[0]
+
+    def result():
+        out = np.empty(n)
+        u.read_sync(out)
+        return out
+    return prepare, issue, result
+
+
+def _case_heat3d(dev, mode):
+    shape = (24, 40, 56)
+    u0 = np.ascontiguousarray(synth.heat3d_input(56, seed=271, nz=24, ny=40), dtype=np.float32)
+    u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+
+    def prepare():
+        u.write(u0).get()
+
+    def issue():
+        return hxc.heat3d_run(dev, u, t, shape, 0.15, 8, mode, 4)[0]
+
+    def result():
+        out = np.empty_like(u0)
+        u.read_sync(out)
+        return out
+    return prepare, issue, result
+
+
+def _case_batch(dev, mode):
+    sides, offs, kap, ub, cs = synth.batch_input(nprob=20, seed=272)
+    bu, bk = dev.buffer(ub.nbytes), dev.buffer(kap.nbytes)
+    bk.write(kap).get()
+
+    def prepare():
+        bu.write(ub).get()
+
+    def issue():
+        return hxc.varcoef_batch_run(dev, bu, bk, sides, cs, 6, mode)[0]
+
+    def result():
+        out = np.empty_like(ub)
+        bu.read_sync(out)
+        return out
+    return prepare, issue, result
+
+
+def _case_adjoint(dev, mode):
+    n = 64
+    kref, kap, u0, c = synth.adjoint_input(n)
+    b0, bk, bl = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    gk, gu, ut = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    b0.write(u0).get()
+    bk.write(kap).get()
+    bl.write(u0).get()
+
+    def prepare():
+        pass
+
+    def issue():
+        return hxc.varcoef_adjoint_run(dev, b0, bk, bl, n, n, c, 30, gk, gu, ut, 0, mode)[0]
+
+    def result():
+        a, b = np.empty_like(u0), np.empty_like(u0)
+        gk.read_sync(a)
+        gu.read_sync(b)
+        return np.concatenate([a.ravel(), b.ravel()])
+    return prepare, issue, result
+
+
+def _case_forward(dev, mode):
+    n = 72
+    kref, kap, u0, c = synth.adjoint_input(n)
+    b0, bk, ut = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    b0.write(u0).get()
+    bk.write(kap).get()
+
+    def prepare():
+        pass
+
+    def issue():
+        return hxc.varcoef_forward_run(dev, b0, bk, n, n, c, 25, ut)[0]
+
+    def result():
+        out = np.empty_like(u0)
+        ut.read_sync(out)
+        return out
+    return prepare, issue, result
+
+
+def _case_stream2d(dev, mode):
+    u0 = synth.bumps2d(70, 90, seed=273, nbumps=3, sigma=0.1)
+    ha, hb = hxc.host_empty(u0.shape), hxc.host_empty(u0.shape)
+    res = {}
+
+    def prepare():
+        ha[:] = u0
+        hb[:] = 0.0
+
+    def issue():
+        f, _, out = hxc.heat2d_stream_run(dev, ha, hb, (2, 2), 0.2, 3, sequential=(mode == "plain"))
+        res["out"] = out
+        return f
+
+    def result():
+        return np.array(res["out"])
+    return prepare, issue, result
+
+
+def _case_partition(dev, mode):
+    n = 1 << 16
+    hx, hr = hxc.host_empty(n), hxc.host_empty(n)
+    work = dev.buffer(n * 8)
+
+    def prepare():
+        hx[:] = np.arange(n, dtype=np.float64)
+        hr[:] = 0.0
+
+    def issue():
+        return hxc.partition_run(dev, hx, hr, 4, work)
+
+    def result():
+        return np.array(hr)
+    return prepare, issue, result
+
+
+CASES = [("heat1d", _case_heat1d, m) for m in ("plain", "graph", "fused")] + \
+        [("heat3d", _case_heat3d, m) for m in ("plain", "graph", "fused")] + \
+        [("batch", _case_batch, m) for m in ("plain", "graph", "fused")] + \
+        [("adjoint", _case_adjoint, m) for m in ("plain", "graph", "fused")] + \
+        [("forward", _case_forward, "fused"), ("stream2d", _case_stream2d, "plain"),
+         ("stream2d", _case_stream2d, "fused"), ("partition", _case_partition, "fused")]
+
+
+@pytest.mark.parametrize("name,case,mode", CASES, ids=["%s-%s" % (c[0], c[2]) for c in CASES])
+def test_every_run_survives_an_injected_failure(dev, name, case, mode):
+    """For every run entry point and mode: a run with one device operation
+    failing at issue reports the failure (synchronously or in its future,
+    within a bounded wait), and the same run afterwards gives the bits of a
+    run that never saw a failure."""
+    prepare, issue, result = case(dev, mode)
+    prepare()
+    f = issue()
+    assert f.wait(WAIT_NS) == hxc.HXC_OK
+    want = result()
+    for after in (0, 3, 11):
+        prepare()
+        hxc.debug_inject(after)
+        try:
+            f = issue()
+            st = f.wait(WAIT_NS)
+            assert st != hxc.HXC_E_TIMEOUT, (after, st)
+        except hxc.HxcError:
+            pass
+        hxc.debug_inject(-1)
+        dev.synchronize()
+        prepare()
+        f = issue()
+        assert f.wait(WAIT_NS) == hxc.HXC_OK, after
+        got = result()
+        assert np.array_equal(got, want), after
