@@ -255,3 +255,13 @@ def test_host_norms_on_the_worker_pool():
     assert np.max(np.abs(got[2:] - want[2:]) / np.array(want[2:])) <= 2e-14
     L = hxc.lib()
     assert L.hxc_host_norms(None, None, 2, None) == hxc.HXC_E_INVALID
+
+
+def test_debug_inject_arguments():
+    """hxc_debug_inject needs a failure status to arm and disarms with a
+    negative count; arming and disarming need no device."""
+    L = hxc.lib()
+    assert L.hxc_debug_inject(ctypes.c_int64(0), hxc.HXC_OK) == hxc.HXC_E_INVALID
+    assert L.hxc_debug_inject(ctypes.c_int64(5), hxc.HXC_E_CUDA) == hxc.HXC_OK
+    assert L.hxc_debug_inject(ctypes.c_int64(-1), hxc.HXC_OK) == hxc.HXC_OK
+    hxc.debug_inject(-1)
