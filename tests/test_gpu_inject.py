@@ -245,7 +245,31 @@ def _case_partition(dev, mode):
     return prepare, issue, result
 
 
+def _case_host2d(dev, mode):
+    """The synchronous host entry point: the field in and out of host memory,
+    snapshots with host norms."""
+    u0 = synth.bumps2d(64, 96, seed=274, nbumps=3, sigma=0.1)
+    hu, ho = hxc.host_empty(u0.shape), hxc.host_empty(u0.shape)
+    hn = np.zeros(2 * 4)
+
+    def prepare():
+        hu[:] = u0
+        ho[:] = 0.0
+
+    def issue():
+        cfg = hxc.heat2d_cfg(64, 96, 2, 2, 0.2, 10, 5, mode, hn, None)
+        hxc.heat2d_run_host(dev, hu.ctypes.data, ho.ctypes.data, cfg)
+        f = hxc.promise()
+        hxc.promise_set(f, hxc.HXC_OK)
+        return f
+
+    def result():
+        return np.concatenate([np.array(ho).ravel(), hn])
+    return prepare, issue, result
+
+
 CASES = [("heat1d", _case_heat1d, m) for m in ("plain", "graph", "fused")] + \
+        [("host2d", _case_host2d, m) for m in ("plain", "graph", "fused")] + \
         [("heat3d", _case_heat3d, m) for m in ("plain", "graph", "fused")] + \
         [("batch", _case_batch, m) for m in ("plain", "graph", "fused")] + \
         [("adjoint", _case_adjoint, m) for m in ("plain", "graph", "fused")] + \
