@@ -108,6 +108,39 @@ __global__ void k_vc_step(const double *__restrict__ u, double *__restrict__ un,
     }
 }
 
+// The same step with two adjacent cells per thread (even nx): 16-byte loads
+// of u, its north/south rows and the coefficients halve the load
+// instructions; warps walk rows, a lane covering columns 2l, 2l+1 of a
+// 64-column segment.  Same canonical update as vc_step_at.
+__global__ void k_vc_step2(const double *__restrict__ u, double *__restrict__ un,
+                           const double *__restrict__ wE, const double *__restrict__ wS,
+                           const double *__restrict__ m, int64_t ny, int64_t nx, Fk f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t segs = (nx + 63) / 64;
+    const double2 z2 = make_double2(0.0, 0.0);
+    for (int64_t w = blockIdx.x * wpb + (threadIdx.x >> 5); w < ny * segs;
+         w += (int64_t)gridDim.x * wpb) {
+        const int64_t i = w / segs, j = (w % segs) * 64 + 2 * lane;
+        if (j >= nx) continue;
+        const int64_t a = i * nx + j;
+        const double2 c = __ldg(reinterpret_cast<const double2 *>(u + a));
+        const double2 no = i > 0 ? __ldg(reinterpret_cast<const double2 *>(u + a - nx)) : z2;
+        const double2 so = i + 1 < ny ? __ldg(reinterpret_cast<const double2 *>(u + a + nx)) : z2;
+        const double uw = j > 0 ? __ldg(u + a - 1) : 0.0;
+        const double ue = j + 2 < nx ? __ldg(u + a + 2) : 0.0;
+        const double2 e = __ldg(reinterpret_cast<const double2 *>(wE + a));
+        const double ww = j > 0 ? __ldg(wE + a - 1) : 0.0;
+        const double2 ss = __ldg(reinterpret_cast<const double2 *>(wS + a));
+        const double2 sn = i > 0 ? __ldg(reinterpret_cast<const double2 *>(wS + a - nx)) : z2;
+        const double2 mm = __ldg(reinterpret_cast<const double2 *>(m + a));
+        double2 o;
+        o.x = vc_update(c.x, uw, c.y, no.x, so.x, ww, e.x, sn.x, ss.x, mm.x, f);
+        o.y = vc_update(c.y, c.x, ue, no.y, so.y, e.x, e.y, sn.y, ss.y, mm.y, f);
+        *reinterpret_cast<double2 *>(un + a) = o;
+    }
+}
+
 // Coefficients computed on the fly (the hxc_launch kernel): same bits.
 __global__ void k_vc_step_otf(const double *__restrict__ u, double *__restrict__ un,
                               const double *__restrict__ kap, double c, int64_t ny, int64_t nx,
@@ -340,6 +373,16 @@ cudaError_t vc_coef(const double *kap, double c, int64_t ny, int64_t nx, double 
 
 cudaError_t vc_step(const double *u, double *un, const double *wE, const double *wS,
                     const double *m, int64_t ny, int64_t nx, cudaStream_t s) {
+    const bool vec = nx % 2 == 0 && reinterpret_cast<uintptr_t>(u) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(un) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(wE) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(wS) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(m) % 16 == 0;
+    if (vec) {
+        const int64_t work2 = ny * ((nx + 63) / 64);
+        k_vc_step2<<<grid_for(work2, 8, nullptr), 256, 0, s>>>(u, un, wE, wS, m, ny, nx, kF);
+        return cudaGetLastError();
+    }
     const int64_t work = ny * ((nx + 31) / 32);
     k_vc_step<<<grid_for(work, 8, nullptr), 256, 0, s>>>(u, un, wE, wS, m, ny, nx, kF);
     return cudaGetLastError();
