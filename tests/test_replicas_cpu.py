@@ -37,12 +37,14 @@ def test_reductions_over_two_gloo_ranks(tmp_path):
         assert bench.allmax(pg, ms) == 15.0
         assert bench.allsum(pg, work) == 3000.0
         # the aggregate rate: all ranks' work over the slowest rank's time
-        print("RATE", bench.allsum(pg, work) / (bench.allmax(pg, ms) / 1e3), flush=True)
+        # (one file per rank: the ranks' stdout lines may interleave)
+        rate = bench.allsum(pg, work) / (bench.allmax(pg, ms) / 1e3)
+        open({str(tmp_path)!r} + "/rate%d" % rank, "w").write(repr(rate))
         pg.destroy_process_group()
     """))
     r = torchrun([str(script)], timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
-    rates = [float(l.split()[1]) for l in r.stdout.splitlines() if l.startswith("RATE")]
+    rates = [float((tmp_path / ("rate%d" % k)).read_text()) for k in range(2)]
     assert rates == [200000.0, 200000.0]
 
 
