@@ -35,9 +35,39 @@ __device__ __forceinline__ Iter step(float x, float y, float cr, float ci) {
 // tests joined into one branch; on an escape the first test that fired, in
 // order, gives the count, so the result is that of testing after every
 // iteration (values past the escape may overflow; they are never used).
+//
+// Where |c|^2 <= 3.99 an escape cannot undo itself: if |z_j| > 2 (to within
+// rounding) then |z_{j+1}| >= |z_j|^2 - |c| > 2.002, far outside rounding, and
+// the orbit keeps growing (three iterations past an escape stay below 1e5,
+// so nothing overflows).  There only the last of every four iterates is
+// tested; when it has escaped, the group is run again from its first
+// iterate with a test after every iteration, which gives the exact count.
 __device__ __forceinline__ int32_t escape_count(float cr, float ci, int32_t max_iter) {
     float x = 0.0f, y = 0.0f;
     int32_t k = 0;
+    if (__fmaf_rn(cr, cr, __fmul_rn(ci, ci)) <= 3.99f) {
+        for (; k + 4 <= max_iter; k += 4) {
+            float px = x, py = y;
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const float xx = __fmul_rn(px, px), yy = __fmul_rn(py, py);
+                const float nx = __fadd_rn(__fsub_rn(xx, yy), cr);
+                py = __fmaf_rn(__fadd_rn(px, px), py, ci);
+                px = nx;
+            }
+            const Iter d = step(px, py, cr, ci);  // tests z_{k+3}
+            if (d.escaped) {
+                for (;; k++) {  // the first escape in z_k .. z_{k+3}
+                    const Iter a = step(x, y, cr, ci);
+                    if (a.escaped) return k;
+                    x = a.x;
+                    y = a.y;
+                }
+            }
+            x = d.x;
+            y = d.y;
+        }
+    }
     for (; k + 4 <= max_iter; k += 4) {
         const Iter a = step(x, y, cr, ci);
         const Iter b = step(a.x, a.y, cr, ci);
