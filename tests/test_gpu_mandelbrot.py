@@ -40,6 +40,12 @@ CASES = [
     (8, 4, F(-2.0), F(-1.0), F(0.4), F(0.5), 1),                     # one tile, max_iter 1
     (1, 1, F(0.0), F(0.0), F(1.0), F(1.0), 7),
     (64, 48, F(-1.9), F(-1.2), F(0.05), F(0.05), 6),                  # groups of 4 + a tail of 2
+    # across |c|^2 = 3.99, where the kernel switches between testing every
+    # fourth iterate and testing every iterate: on the circle near c = -2
+    # (slow escapes along the real axis), near 1.41 + 1.41i and near 2i
+    (200, 120, F(-2.02), F(-0.03), F(2.5e-4), F(5e-4), 700),
+    (150, 150, F(1.395), F(1.395), F(1e-4), F(1e-4), 300),
+    (160, 100, F(-0.04), F(1.985), F(5e-4), F(2e-4), 300),
 ]
 
 
