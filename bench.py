@@ -328,7 +328,9 @@ def ours(args, world, rank, local, pg):
                "steps": k}
 
     sec = None
-    if not args.quick and not args.no_secondary:
+    # the secondary workloads are reported by rank 0 only (no collective in
+    # them), so the other replicas skip them
+    if not args.quick and not args.no_secondary and rank == 0:
         sec = secondary(dev, timer, peaks)
 
     out = {
