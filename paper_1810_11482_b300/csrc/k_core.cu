@@ -194,11 +194,9 @@ cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_
     if (C + 2 * steps > max_w) C = std::max<int64_t>(16, (max_w - 2 * steps) / 16 * 16);
     if (C + 2 * steps > max_w) return cudaErrorInvalidValue;
     size_t smem = 2 * (size_t)(C + 2 * steps) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_heat1d_tb, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin(k_heat1d_tb, 227 * 1024, attr);
+    if (e != cudaSuccess) return e;
     k_heat1d_tb<<<g, b, smem, s>>>(src, dst, n, lo, count, r, steps, (int)C, 1.0);
     return cudaGetLastError();
 }

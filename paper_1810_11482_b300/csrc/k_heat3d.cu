@@ -626,13 +626,9 @@ template <int T>
 cudaError_t v3_launch(unsigned g, const float *src, float *dst, int nz, int ny, int nx, float r,
                       cudaStream_t s) {
     constexpr size_t smem = sizeof(f2) * 2 * T * V3_NW * 2 * 32;
-    static bool attr = false;  // idempotent, so a race between first callers is harmless
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_heat3d_v3<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin(k_heat3d_v3<T>, (int)smem, attr);
+    if (e != cudaSuccess) return e;
     k_heat3d_v3<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r);
     return cudaGetLastError();
 }
@@ -827,13 +823,9 @@ template <int T>
 cudaError_t v4_launch(unsigned g, const float *src, float *dst, int nz, int ny, int nx, float r,
                       cudaStream_t s) {
     constexpr size_t smem = v4_smem_bytes<T>();
-    static bool attr = false;  // idempotent, so a race between first callers is harmless
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_heat3d_v4<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin(k_heat3d_v4<T>, (int)smem, attr);
+    if (e != cudaSuccess) return e;
     k_heat3d_v4<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r);
     return cudaGetLastError();
 }

@@ -2,6 +2,7 @@
 // the C ABI layer validates sizes and handles before calling these.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -19,6 +20,21 @@ constexpr int kNormBands = 64;
 constexpr size_t kNormScratchBytes = kNormBands * sizeof(double) + 16;
 
 int sm_count();
+
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` once per device
+// (the attribute belongs to the function as loaded on each device); `done`
+// is the caller's static mask of the devices already set.
+template <typename Kernel>
+cudaError_t smem_optin(Kernel *kernel, int bytes, std::atomic<uint64_t> &done) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (d & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 cudaError_t sum_u32(const uint32_t *in, unsigned long long *result, int64_t n,
                     const hxc_launch_cfg *cfg, cudaStream_t s);
