@@ -23,13 +23,17 @@
 namespace hxc {
 namespace k {
 
+// SM count of the current device (cached per device ordinal).
 int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int d = 0;
-        cudaGetDevice(&d);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
-        if (n <= 0) n = 148;
+    static std::atomic<int> cache[64];
+    int d = 0;
+    cudaGetDevice(&d);
+    std::atomic<int> &c = cache[d & 63];
+    int n = c.load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0)
+            n = 148;
+        c.store(n, std::memory_order_relaxed);
     }
     return n;
 }
