@@ -575,6 +575,9 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *                  planes copied into a shared-memory ring two planes ahead
  *                  (default).  Forms 3 and 4 launched with an hxc_launch_cfg
  *                  take 512 threads per CTA and any grid.
+ *   "heat3d.variant1"  the form used for one-step launches (PLAIN mode and
+ *                  single-step remainders), same values (default 0: with a
+ *                  single level the copied-plane form is the fastest).
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
  *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).

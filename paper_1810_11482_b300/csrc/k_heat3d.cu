@@ -866,7 +866,9 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
     const int blocks = heat3d_blocks(nz, ny, nx, steps, zchunk);
     unsigned g = cfg ? cfg->grid[0] * cfg->grid[1] * cfg->grid[2] : (unsigned)blocks;
     // variant 3 keeps in-plane offsets in 32 bits; larger planes take variant 2 (same bits)
-    const int64_t variant = tune::get("heat3d.variant");
+    // one-step launches have a knob of their own: with a single level the
+    // copied-plane form streams faster than the two-plane forms
+    const int64_t variant = tune::get(steps == 1 ? "heat3d.variant1" : "heat3d.variant");
     if (variant >= 3 && (uint64_t)ny * (uint64_t)nx <= 0xffffffffull) {
         if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != V3_NW * 32)
             return cudaErrorInvalidValue;

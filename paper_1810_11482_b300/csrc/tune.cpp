@@ -30,6 +30,7 @@ Knob g_knobs[] = {
     {"heat2d.occupancy", 4, 4, 6},    // compiled minimum of CTAs per SM
     {"heat3d.zchunks", 0, 0, 64},     // z chunks per launch (0: fill whole waves)
     {"heat3d.variant", 4, 0, 4},      // 0 copied, 1 rotated, 2 rotated + f32x2, 3 two-plane, 4 + ring
+    {"heat3d.variant1", 0, 0, 4},     // the same choice for one-step launches
     {"heat1d.tb_ctas", 0, 0, 1 << 16},  // CTAs per partition of the 1D blocked kernel (0: SMs/parts)
     {"batch.ctas_per_sm", 4, 1, 16},  // CTAs per SM of the persistent batch kernel
     {"batch.block", 256, 256, 1024},  // threads per CTA of the persistent batch kernel

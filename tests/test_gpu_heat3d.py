@@ -78,10 +78,11 @@ def test_heat3d_translation_and_reflection_exact(dev):
     shape = (37, 150, 200)
     u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=350, nz=shape[0], ny=shape[1]),
                               dtype=np.float32)
-    old = hxc.tune_get("heat3d.variant")
+    old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1")}
     try:
         for variant in (2, 3, 4):
             hxc.tune_set("heat3d.variant", variant)
+            hxc.tune_set("heat3d.variant1", variant)
             ref, _ = run3d(dev, u0, 8, "fused", 4)
             for sh in ((5, 0, 0), (0, 61, 0), (0, 0, 77), (19, 100, 3)):
                 got, _ = run3d(dev, np.roll(u0, sh, axis=(0, 1, 2)), 8, "fused", 4)
@@ -91,7 +92,8 @@ def test_heat3d_translation_and_reflection_exact(dev):
             got, _ = run3d(dev, u0[:, :, ::-1].copy(), 8, "fused", 4)
             assert np.array_equal(got, ref[:, :, ::-1]), variant
     finally:
-        hxc.tune_set("heat3d.variant", old)
+        for k, v in old.items():
+            hxc.tune_set(k, v)
 
 
 @pytest.mark.parametrize("shape", [(40, 72, 96), (9, 70, 131), (8, 8, 8), (21, 33, 64)])
@@ -104,10 +106,11 @@ def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     u0 = synth.heat3d_input(shape[2], seed=330 + shape[0], nz=shape[0], ny=shape[1])
     ref, _ = run3d(dev, u0, 9, "plain", 1)
     want = oracle.heat3d(u0.astype(np.float64), float(R), 9)
-    old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.zchunks")}
+    old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1", "heat3d.zchunks")}
     try:
         for variant in (0, 1, 2, 3, 4):
             hxc.tune_set("heat3d.variant", variant)
+            hxc.tune_set("heat3d.variant1", variant)
             for nch in (0, 1, 3):
                 hxc.tune_set("heat3d.zchunks", nch)
                 for mode, spl in (("fused", 4), ("fused", 3), ("graph", 4)):
@@ -176,7 +179,7 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
     bits of the copied-plane form (variant 0); 1..4 steps per launch."""
     u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=340 + shape[0], nz=shape[0],
                                                  ny=shape[1]), dtype=np.float32)
-    old = hxc.tune_get("heat3d.variant")
+    old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1")}
     a, b = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
     try:
         for steps in (1, 2, 3, 4):
@@ -184,6 +187,7 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
             for variant, grid in ((0, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000),
                                   (4, None), (4, 1), (4, 7), (4, 100000)):
                 hxc.tune_set("heat3d.variant", variant)
+                hxc.tune_set("heat3d.variant1", variant)
                 a.write(u0).get()
                 args = hxc.hxc_heat3d_args(a.h, b.h, shape[0], shape[1], shape[2], R, steps)
                 cfg = None if grid is None else hxc.hxc_launch_cfg((grid, 1, 1), (512, 1, 1))
@@ -202,4 +206,5 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
         with pytest.raises(hxc.HxcError):
             dev.launch(hxc.HXC_K_HEAT3D, args, cfg=hxc.hxc_launch_cfg((4, 1, 1), (256, 1, 1))).get()
     finally:
-        hxc.tune_set("heat3d.variant", old)
+        for k, v in old.items():
+            hxc.tune_set(k, v)
