@@ -580,6 +580,9 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *                  single level the copied-plane form is the fastest).
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
+ *   "mandel.pair"  Mandelbrot kernel form: 1 = two horizontally adjacent
+ *                  pixels per thread on paired FP32 instructions (default),
+ *                  0 = one pixel per thread.
  *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).
  *   "batch.block"  threads per CTA of the persistent batch kernel: 256 (default),
  *                  512 or 1024; blocks x CTAs per SM must fit the SM.

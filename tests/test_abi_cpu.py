@@ -228,7 +228,7 @@ def test_shipped_tuning_cache_parses(L):
     assert "sm_103" in data and set(data["sm_103"]) <= {"heat2d.emul", "heat2d.rows",
                                                         "heat2d.occupancy", "heat3d.zchunks",
                                                         "heat3d.variant", "heat3d.variant1",
-                                                        "heat1d.tb_ctas",
+                                                        "heat1d.tb_ctas", "mandel.pair",
                                                         "batch.ctas_per_sm", "batch.block"}
     hxc.tune_load(path, 10, 3)
     for k, v in data["sm_103"].items():

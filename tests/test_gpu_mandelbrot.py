@@ -58,6 +58,22 @@ def test_kernel_matches_oracle(dev, case):
     assert np.array_equal(rgb, want_rgb)
 
 
+@pytest.mark.parametrize("case", CASES)
+def test_one_and_two_pixel_forms_agree(dev, case):
+    """The kernel's two forms (one pixel per thread; two adjacent pixels per
+    thread on paired FP32 instructions) give the same counts and colours."""
+    w, h, x0, y0, dx, dy, it = case
+    old = hxc.tune_get("mandel.pair")
+    try:
+        outs = []
+        for pair in (0, 1):
+            hxc.tune_set("mandel.pair", pair)
+            outs.append(device_image(dev, w, h, x0, y0, dx, dy, it))
+        assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][0], outs[1][0])
+    finally:
+        hxc.tune_set("mandel.pair", old)
+
+
 def test_launch_shapes_do_not_change_bits(dev):
     w, h, x0, y0, dx, dy, it = CASES[0]
     a = device_image(dev, w, h, x0, y0, dx, dy, it)
