@@ -464,6 +464,21 @@ hxc_status hxc_heat2d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, const hx
  * host_u0).  Synchronous: returns when host_uT and the norms are written. */
 hxc_status hxc_heat2d_run_host(hxc_device dev, const double *host_u0, double *host_uT,
                                const hxc_heat2d_cfg *cfg, hxc_run_stats *stats);
+/* The asynchronous form: the uploads start after `deps`; *out completes
+ * when host_uT holds the result and the run (its norms included) is done.
+ * The library keeps two device field pairs per device for these calls and
+ * gives them out in turn, so the uploads and downloads of one call overlap
+ * the steps of the call issued before it; a call's uploads wait (on the
+ * device) for the downloads of the call issued two before it, the last user
+ * of its pair.  host_u0 must stay valid and host_uT untouched until *out is
+ * ready; both should be page-locked (hxc_host_alloc) for the copies to
+ * overlap.  Calls whose snapshot norms go to the same arrays must not
+ * overlap (each run writes every entry).  Argument errors are returned
+ * synchronously with no future created; a failure of a copy or of the run
+ * is stored in *out and does not affect later calls. */
+hxc_status hxc_heat2d_run_host_async(hxc_device dev, const double *host_u0, double *host_uT,
+                                     const hxc_heat2d_cfg *cfg, const hxc_future *deps,
+                                     int ndeps, hxc_future *out, hxc_run_stats *stats);
 
 /* 3D periodic FTCS in FP32 on an nz x ny x nx field (x fastest): u holds
  * the initial field and receives the result, tmp is scratch of the same

@@ -479,13 +479,31 @@ struct RingCarry {
 std::mutex g_carry_m;
 std::map<Device *, RingCarry> g_carry;
 
+// Two device field pairs per device for the host entry points, used in turn:
+// the uploads and downloads of one call overlap the steps of the call issued
+// before it, and a call waits (on the device) only for the call two back,
+// the last user of its pair.
+struct HostRunSlots {
+    int next = 0;
+    FutRef last[2];
+};
+std::mutex g_hostrun_m;
+std::map<Device *, HostRunSlots> g_hostrun;
+const char *const kHostKeyU[2] = {"heat2d_host.u0", "heat2d_host.u1"};
+const char *const kHostKeyT[2] = {"heat2d_host.t0", "heat2d_host.t1"};
+constexpr int kHostSlots = 8;
+constexpr int kHostInSlot0 = kCopySlot0 + kCopySlots;     // host-run uploads
+constexpr int kHostOutSlot0 = kHostInSlot0 + kHostSlots;  // host-run downloads
+static_assert(kHostOutSlot0 + kHostSlots <= HXC_MAX_SLOTS, "stream slots");
+
 // Page-locked staging of the device norms, per device; `last` is the host
 // copy of the previous run that read it.
 struct GnormStage {
     std::mutex m;
     void *ptr = nullptr;
     size_t bytes = 0;
-    FutRef last;
+    FutRef last;    // the host copy of the last run's norms into the caller's array
+    FutRef copied;  // the device->host copy of its device norm rows
 };
 GnormStage &gnorm_stage(Device *d) {
     static std::mutex mm;
@@ -626,6 +644,13 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             return st;
     }
 
+    // the device norm rows are shared by the runs on this device: this run
+    // writes them only after the last run's rows have been copied out
+    if (cfg->gpu_norms && want_snaps) {
+        GnormStage &gs = gnorm_stage(d.get());
+        std::lock_guard<std::mutex> lk(gs.m);
+        if (FutRef c = fut_order_only(gs.copied)) dv.push_back(c);
+    }
     Ref<RunResources> res(new RunResources(), true);
     res->keep = {AnyRef(u.get(), false), AnyRef(tb.get(), false)};
     std::vector<FutRef> prev(T);
@@ -805,6 +830,7 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
                                   {}, &c)))
             return st;
         R.stats.copy(0, bytes);
+        gs.copied = c;
         double *dst = cfg->gpu_norms;
         FutRef r = make_pending();
         fut_on_done(c, [r, stage, dst, bytes](hxc_status s2) {
@@ -857,22 +883,41 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
 
 extern "C" {
 
-hxc_status hxc_heat2d_run_host(hxc_device dh, const double *host_u0, double *host_uT,
-                               const hxc_heat2d_cfg *cfg, hxc_run_stats *stats_out) {
+hxc_status hxc_heat2d_run_host_async(hxc_device dh, const double *host_u0, double *host_uT,
+                                     const hxc_heat2d_cfg *cfg, const hxc_future *deps, int ndeps,
+                                     hxc_future *out, hxc_run_stats *stats_out) {
     Ref<Device> d = dev_from_handle(dh);
     if (!d) return HXC_E_INVALID;
-    if (!cfg || !host_u0 || !host_uT || cfg->ny <= 0 || cfg->nx <= 0 || cfg->tiles_y < 1 ||
-        cfg->tiles_x < 1 || cfg->tiles_y > cfg->ny || cfg->tiles_x > cfg->nx ||
-        cfg->tiles_y * cfg->tiles_x > kCopySlot0) {
+    if (!cfg || !host_u0 || !host_uT || !out || cfg->ny <= 0 || cfg->nx <= 0 ||
+        cfg->tiles_y < 1 || cfg->tiles_x < 1 || cfg->tiles_y > cfg->ny ||
+        cfg->tiles_x > cfg->nx || cfg->tiles_y * cfg->tiles_x > kCopySlot0) {
         set_error("hxc_heat2d_run_host: invalid arguments");
         return HXC_E_INVALID;
     }
-    hxc_status st = d->make_current();
+    std::vector<FutRef> dv;
+    hxc_status st = deps_from_handles(deps, ndeps, &dv);
     if (st) return st;
+    if ((st = d->make_current())) return st;
     const size_t field = (size_t)cfg->ny * cfg->nx * 8;
+    // the device field pair of this call, and the call that used it last
+    int slot;
+    FutRef prev;
+    {
+        std::lock_guard<std::mutex> g(g_hostrun_m);
+        HostRunSlots &hs = g_hostrun[d.get()];
+        slot = hs.next;
+        hs.next ^= 1;
+        prev = hs.last[slot];
+    }
+    // a pair that has to grow is freed and reallocated: its last user must
+    // be done with it, including work still to be issued from the pool
+    if (prev && !d->scratch_fits(kHostKeyU[slot], field)) {
+        fut_wait(prev, -1);
+        prev = FutRef();
+    }
     void *pu, *pt;
-    if ((st = d->scratch_get("heat2d_host.u", field, &pu))) return st;
-    if ((st = d->scratch_get("heat2d_host.t", field, &pt))) return st;
+    if ((st = d->scratch_get(kHostKeyU[slot], field, &pu))) return st;
+    if ((st = d->scratch_get(kHostKeyT[slot], field, &pt))) return st;
     hxc_buffer ub, tb;
     hxc_buffer_wrap(dh, pu, field, &ub);
     hxc_buffer_wrap(dh, pt, field, &tb);
@@ -883,47 +928,88 @@ hxc_status hxc_heat2d_run_host(hxc_device dh, const double *host_u0, double *hos
     tl.bx = split(cfg->nx, cfg->tiles_x, true);
     const int64_t T = tl.count(), nx = cfg->nx;
     hxc_run_stats inner{};
-    std::vector<hxc_future> h2d(T);
-    for (int64_t t = 0; t < T; t++) {
+    std::vector<hxc_future> in_deps;
+    for (auto &f : dv) in_deps.push_back(to_handle(f));
+    if (prev) in_deps.push_back(to_handle(prev));
+    std::vector<hxc_future> h2d, d2h;
+    hxc_future run = nullptr, ready = nullptr;
+    auto cleanup = [&]() {
+        for (auto f : in_deps) hxc_future_release(f);
+        for (auto f : h2d) hxc_future_release(f);
+        for (auto f : d2h) hxc_future_release(f);
+        if (run) hxc_future_release(run);
+        if (ready) hxc_future_release(ready);
+        hxc_buffer_release(ub);
+        hxc_buffer_release(tb);
+    };
+    // uploads and downloads on their own stream slots, so that they overlap
+    // the steps of the call issued before this one
+    for (int64_t t = 0; t < T && !st; t++) {
         size_t off = ((size_t)tl.y0(t) * nx + tl.x0(t)) * 8;
+        hxc_future f = nullptr;
         st = hxc_buffer_enqueue_write_2d(ub, off, nx * 8, (const char *)host_u0 + off, nx * 8,
-                                         tl.tx(t) * 8, tl.ty(t), (int)t, nullptr, 0, &h2d[t]);
-        if (st) return st;
+                                         tl.tx(t) * 8, tl.ty(t), kHostInSlot0 + (int)(t % kHostSlots),
+                                         in_deps.data(), (int)in_deps.size(), &f);
+        if (!st) h2d.push_back(f);
         inner.copies++;
         inner.h2d_bytes += tl.tx(t) * tl.ty(t) * 8;
     }
-    hxc_future run = nullptr, ready = nullptr;
     hxc_run_stats rs{};
-    st = hxc_heat2d_run(dh, ub, tb, cfg, h2d.data(), (int)T, &run, &ready, &rs);
-    for (auto f : h2d) hxc_future_release(f);
-    if (st) {
-        hxc_buffer_release(ub);
-        hxc_buffer_release(tb);
-        return st;
-    }
-    std::vector<hxc_future> d2h(T);
-    for (int64_t t = 0; t < T; t++) {
+    if (!st) st = hxc_heat2d_run(dh, ub, tb, cfg, h2d.data(), (int)T, &run, &ready, &rs);
+    for (int64_t t = 0; t < T && !st; t++) {
         size_t off = ((size_t)tl.y0(t) * nx + tl.x0(t)) * 8;
+        hxc_future f = nullptr;
         st = hxc_buffer_enqueue_read_2d(ub, off, nx * 8, (char *)host_uT + off, nx * 8,
-                                        tl.tx(t) * 8, tl.ty(t), (int)t, &ready, 1, &d2h[t]);
-        if (st) return st;
+                                        tl.tx(t) * 8, tl.ty(t), kHostOutSlot0 + (int)(t % kHostSlots),
+                                        &ready, 1, &f);
+        if (!st) d2h.push_back(f);
         inner.copies++;
         inner.d2h_bytes += tl.tx(t) * tl.ty(t) * 8;
     }
-    hxc_status w = hxc_wait_all(d2h.data(), (int)T, -1);
-    hxc_status w2 = hxc_future_wait(run, -1);
-    for (auto f : d2h) hxc_future_release(f);
-    hxc_future_release(run);
-    hxc_future_release(ready);
-    hxc_buffer_release(ub);
-    hxc_buffer_release(tb);
+    hxc_future all = nullptr;
+    if (!st) {
+        d2h.push_back(run);
+        run = nullptr;
+        st = hxc_when_all(d2h.data(), (int)d2h.size(), &all);
+    }
+    if (st) {
+        // nothing more is issued into this pair; its next user waits for
+        // whatever did get issued
+        std::vector<hxc_future> issued(h2d);
+        issued.insert(issued.end(), d2h.begin(), d2h.end());
+        if (run) issued.push_back(run);
+        hxc_future j = nullptr;
+        if (!issued.empty() && hxc_when_all(issued.data(), (int)issued.size(), &j) == HXC_OK) {
+            std::lock_guard<std::mutex> g(g_hostrun_m);
+            g_hostrun[d.get()].last[slot] = fut_order_only(fut_from_handle(j));
+            hxc_future_release(j);
+        }
+        cleanup();
+        return st;
+    }
+    {
+        std::lock_guard<std::mutex> g(g_hostrun_m);
+        g_hostrun[d.get()].last[slot] = fut_order_only(fut_from_handle(all));
+    }
+    cleanup();
     if (stats_out) {
         *stats_out = rs;
         stats_out->copies += inner.copies;
         stats_out->h2d_bytes += inner.h2d_bytes;
         stats_out->d2h_bytes += inner.d2h_bytes;
     }
-    return w ? w : w2;
+    *out = all;
+    return HXC_OK;
+}
+
+hxc_status hxc_heat2d_run_host(hxc_device dh, const double *host_u0, double *host_uT,
+                               const hxc_heat2d_cfg *cfg, hxc_run_stats *stats_out) {
+    hxc_future f = nullptr;
+    hxc_status st = hxc_heat2d_run_host_async(dh, host_u0, host_uT, cfg, nullptr, 0, &f, stats_out);
+    if (st) return st;
+    st = hxc_future_wait(f, -1);
+    hxc_future_release(f);
+    return st;
 }
 
 

@@ -484,7 +484,6 @@ __global__ void __launch_bounds__(256) k_tile_norm_grid(const double *__restrict
         double sm = 0.0;
         for (int b = 0; b < kNormBands; b++) sm = __dadd_rn(sm, __ldcg(part + b));
         norms[tile] = __dsqrt_rn(sm);
-        *counter = 0u;  // leave the scratch ready for the next launch
     }
 }
 
@@ -493,6 +492,11 @@ cudaError_t tile_norm_grid(const double *src, double *snap, int64_t snap_stride,
                            cudaStream_t s) {
     double *partials = static_cast<double *>(scratch);
     unsigned *counters = reinterpret_cast<unsigned *>(partials + TY * TX * kNormBands);
+    // the counters sit behind the partials, so their place moves with the
+    // tile count: clear them for every launch (the scratch is shared by runs
+    // of any tile grid)
+    cudaError_t e = cudaMemsetAsync(counters, 0, (size_t)TY * TX * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     dim3 grid(kNormBands, (unsigned)(TY * TX));
     k_tile_norm_grid<<<grid, 256, 0, s>>>(src, snap, snap_stride, norms, partials, counters, ny,
                                           nx, TY, TX);

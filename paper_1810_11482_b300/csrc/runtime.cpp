@@ -171,6 +171,12 @@ void Device::put_event(cudaEvent_t e) {
     free_events.push_back(e);
 }
 
+bool Device::scratch_fits(const std::string &key, size_t bytes) {
+    std::lock_guard<std::mutex> g(m);
+    auto it = scratch.find(key);
+    return it != scratch.end() && it->second.second >= bytes;
+}
+
 hxc_status Device::scratch_get(const std::string &key, size_t bytes, void **p) {
     std::lock_guard<std::mutex> g(m);
     auto it = scratch.find(key);

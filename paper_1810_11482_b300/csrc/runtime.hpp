@@ -127,6 +127,8 @@ struct Device : RefCounted {
     // Device memory cached under `key`, at least `bytes` large, zero-filled
     // when first allocated.  Valid until the device is destroyed.
     hxc_status scratch_get(const std::string &key, size_t bytes, void **p);
+    // True if scratch_get(key, bytes) would return the current allocation.
+    bool scratch_fits(const std::string &key, size_t bytes);
 };
 
 struct Buffer : RefCounted {

@@ -245,6 +245,10 @@ _SIGS = {
                                       ctypes.c_void_p]),
     "hxc_heat2d_run_host": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.POINTER(hxc_heat2d_cfg), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_heat2d_run_host_async": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(hxc_heat2d_cfg), ctypes.POINTER(c_fut),
+                                         ctypes.c_int, ctypes.POINTER(c_fut),
+                                         ctypes.POINTER(hxc_run_stats)]),
 }
 
 _lib = None
@@ -555,6 +559,18 @@ def heat2d_run_host(dev, host_u0, host_uT, cfg):
     check(lib().hxc_heat2d_run_host(dev.h, host_u0, host_uT, ctypes.byref(cfg),
                                     ctypes.byref(st)), "heat2d_run_host")
     return st
+
+
+def heat2d_run_host_async(dev, host_u0, host_uT, cfg, deps=()):
+    """Returns (future of the result in host_uT and the norms, stats).  The
+    host arrays and cfg (with its norm arrays) must outlive the future."""
+    arr, nd = _futs(deps)
+    out = c_fut()
+    st = hxc_run_stats()
+    check(lib().hxc_heat2d_run_host_async(dev.h, host_u0, host_uT, ctypes.byref(cfg), arr, nd,
+                                          ctypes.byref(out), ctypes.byref(st)),
+          "heat2d_run_host_async")
+    return Future(out.value), st
 
 
 class _Pinned:

@@ -269,6 +269,15 @@ def test_heat2d_snapshot_norms(dev):
     assert np.array_equal(g1, g2) and np.array_equal(g1, g3)
 
 
+def test_heat2d_device_norms_when_the_tile_count_changes(dev):
+    """Fused runs share one reduction scratch whatever their tile grid:
+    device norms stay right when the tile count goes down and up again."""
+    u0 = synth.bumps2d(192, 240, seed=221, nbumps=5, sigma=0.06)
+    for tiles in ((4, 5), (2, 3), (4, 5), (3, 4), (1, 1), (2, 3)):
+        _, hn, gn, _ = run2d(dev, u0, tiles, 0.2, 12, "fused", 6)
+        assert np.max(np.abs(gn - hn) / hn) <= 1e-13, tiles
+
+
 def test_heat2d_full_config(dev):
     """8192^2, 64 tiles of 1024^2, r = 0.2, 1000 steps, snapshots every 100
     steps: every mode bit-identical; a corner window checked against the
@@ -341,6 +350,67 @@ def test_heat2d_host_entry_point(dev):
     want = oracle.heat2d(u0, 0.2, 40)
     assert relerr(np.array(out), want) <= TOL
     assert st.h2d_bytes == u0.nbytes and st.d2h_bytes >= u0.nbytes
+
+
+def test_heat2d_host_async_calls_overlap_and_match(dev):
+    """hxc_heat2d_run_host_async: five calls issued back to back on different
+    fields, two shapes (a device field pair grows while the other call is in
+    flight), each result and each norm bit-identical to the synchronous entry
+    point and the field within the oracle's tolerance."""
+    shapes = [(512, 384), (512, 384), (640, 512), (512, 384), (640, 512)]
+    fields = [synth.bumps2d(ny, nx, seed=600 + i, nbumps=5, sigma=0.06)
+              for i, (ny, nx) in enumerate(shapes)]
+    keep, futs = [], []
+    for i, u0 in enumerate(fields):
+        hu, ho = hxc.host_empty(u0.shape), hxc.host_empty(u0.shape)
+        hu[:] = u0
+        ho[:] = np.nan
+        hn, gn = np.zeros(2 * 6), np.zeros(2 * 6)
+        mode = ("fused", "plain", "graph")[i % 3]
+        cfg = hxc.heat2d_cfg(u0.shape[0], u0.shape[1], 2, 3, 0.2, 30, 15, mode, hn, gn)
+        f, st = hxc.heat2d_run_host_async(dev, hu.ctypes.data, ho.ctypes.data, cfg)
+        assert st.h2d_bytes == u0.nbytes and st.d2h_bytes >= u0.nbytes
+        keep.append((hu, ho, hn, gn, cfg))
+        futs.append(f)
+    for f in futs:
+        assert f.wait(60 * 10**9) == hxc.HXC_OK
+    for i, u0 in enumerate(fields):
+        hu, ho, hn, gn, _ = keep[i]
+        out = hxc.host_empty(u0.shape)
+        hn2, gn2 = np.zeros(12), np.zeros(12)
+        cfg = hxc.heat2d_cfg(u0.shape[0], u0.shape[1], 2, 3, 0.2, 30, 15, "fused", hn2, gn2)
+        hxc.heat2d_run_host(dev, hu.ctypes.data, out.ctypes.data, cfg)
+        assert np.array_equal(np.array(ho).view(np.uint64), np.array(out).view(np.uint64)), i
+        assert np.array_equal(hn, hn2) and np.array_equal(gn, gn2), i
+        assert relerr(np.array(ho), oracle.heat2d(u0, 0.2, 30)) <= TOL
+
+
+def test_heat2d_host_async_dependencies_and_failure(dev):
+    """The uploads of an asynchronous host call wait for its dependencies; a
+    failed dependency fails that call only, and the next calls (which reuse
+    its device field pair) run normally."""
+    ny, nx = 256, 320
+    u0 = synth.bumps2d(ny, nx, seed=610, nbumps=4, sigma=0.08)
+    want = oracle.heat2d(u0, 0.2, 12)
+    hu = hxc.host_empty((ny, nx))
+    hu[:] = u0
+    outs = [hxc.host_empty((ny, nx)) for _ in range(3)]
+    hn = np.zeros(2 * 4)
+    cfg = hxc.heat2d_cfg(ny, nx, 2, 2, 0.2, 12, 6, "fused", hn, None)
+    gate = hxc.promise()
+    f0, _ = hxc.heat2d_run_host_async(dev, hu.ctypes.data, outs[0].ctypes.data, cfg, deps=[gate])
+    assert f0.wait(50 * 10**6) == hxc.HXC_E_TIMEOUT  # held by the gate
+    hxc.promise_set(gate, hxc.HXC_OK)
+    assert f0.wait(60 * 10**9) == hxc.HXC_OK
+    assert relerr(np.array(outs[0]), want) <= TOL
+    bad = hxc.promise()
+    f1, _ = hxc.heat2d_run_host_async(dev, hu.ctypes.data, outs[1].ctypes.data, cfg, deps=[bad])
+    hxc.promise_set(bad, hxc.HXC_E_CALLBACK)
+    assert f1.wait(60 * 10**9) == hxc.HXC_E_DEP_FAILED
+    for i in range(3):
+        f, _ = hxc.heat2d_run_host_async(dev, hu.ctypes.data, outs[2].ctypes.data, cfg)
+        assert f.wait(60 * 10**9) == hxc.HXC_OK, i
+        assert np.array_equal(np.array(outs[2]), np.array(outs[0])), i
 
 
 # ------------------------------------------- integer-pipe FP64 additions
