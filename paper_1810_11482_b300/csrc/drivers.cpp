@@ -821,7 +821,8 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
         double *stage = static_cast<double *>(gs.ptr);
         const double *src = R.norm_dev;
         std::vector<FutRef> cdeps = finals;
-        if (gs.last) cdeps.push_back(gs.last);  // the previous run's host copy is done
+        // the previous run's host copy is done (order only: its failure is not this run's)
+        if (FutRef o = fut_order_only(gs.last)) cdeps.push_back(o);
         FutRef c;
         if ((st = issue_device_op(d.get(), kCopySlot0, cdeps,
                                   [=](cudaStream_t s) {
@@ -908,12 +909,6 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dh, const double *host_u0, doubl
         slot = hs.next;
         hs.next ^= 1;
         prev = hs.last[slot];
-    }
-    // a pair that has to grow is freed and reallocated: its last user must
-    // be done with it, including work still to be issued from the pool
-    if (prev && !d->scratch_fits(kHostKeyU[slot], field)) {
-        fut_wait(prev, -1);
-        prev = FutRef();
     }
     void *pu, *pt;
     if ((st = d->scratch_get(kHostKeyU[slot], field, &pu))) return st;

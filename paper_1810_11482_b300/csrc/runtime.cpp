@@ -120,6 +120,7 @@ Device::~Device() {
     if (cap_fork) cudaEventDestroy(cap_fork);
     for (auto e : free_events) cudaEventDestroy(e);
     for (auto &kv : scratch) cudaFree(kv.second.first);
+    for (auto p : retired) cudaFree(p);
 }
 
 hxc_status Device::stream(int slot, cudaStream_t *s) {
@@ -171,12 +172,6 @@ void Device::put_event(cudaEvent_t e) {
     free_events.push_back(e);
 }
 
-bool Device::scratch_fits(const std::string &key, size_t bytes) {
-    std::lock_guard<std::mutex> g(m);
-    auto it = scratch.find(key);
-    return it != scratch.end() && it->second.second >= bytes;
-}
-
 hxc_status Device::scratch_get(const std::string &key, size_t bytes, void **p) {
     std::lock_guard<std::mutex> g(m);
     auto it = scratch.find(key);
@@ -187,8 +182,9 @@ hxc_status Device::scratch_get(const std::string &key, size_t bytes, void **p) {
     hxc_status st = make_current();
     if (st) return st;
     if (it != scratch.end()) {
-        cudaDeviceSynchronize();
-        cudaFree(it->second.first);
+        // operations already issued, or still to be issued from the worker
+        // pool, may hold the old pointer: it is kept until the device goes
+        retired.push_back(it->second.first);
         scratch.erase(it);
     }
     void *q = nullptr;

@@ -117,6 +117,7 @@ struct Device : RefCounted {
     std::atomic<int> deferred{0};
     // scratch allocations cached by key (released with the device)
     std::unordered_map<std::string, std::pair<void *, size_t>> scratch;
+    std::vector<void *> retired;  // outgrown scratch, freed with the device
 
     ~Device() override;
     hxc_status make_current();
@@ -125,10 +126,9 @@ struct Device : RefCounted {
     cudaEvent_t get_event();
     void put_event(cudaEvent_t e);
     // Device memory cached under `key`, at least `bytes` large, zero-filled
-    // when first allocated.  Valid until the device is destroyed.
+    // when first allocated.  Valid until the device is destroyed, also after
+    // a larger request for the same key has replaced it.
     hxc_status scratch_get(const std::string &key, size_t bytes, void **p);
-    // True if scratch_get(key, bytes) would return the current allocation.
-    bool scratch_fits(const std::string &key, size_t bytes);
 };
 
 struct Buffer : RefCounted {

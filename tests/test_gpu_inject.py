@@ -245,6 +245,29 @@ def _case_partition(dev, mode):
     return prepare, issue, result
 
 
+def _case_heat2d(dev, mode):
+    """The resident 2D run with host and device norms."""
+    u0 = synth.bumps2d(72, 100, seed=275, nbumps=3, sigma=0.1)
+    u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    hn, gn = np.zeros(3 * 6), np.zeros(3 * 6)
+
+    def prepare():
+        u.write(u0).get()
+        hn[:] = 0.0
+        gn[:] = 0.0
+
+    def issue():
+        cfg = hxc.heat2d_cfg(72, 100, 2, 3, 0.2, 12, 4, mode, hn, gn)
+        issue.cfg = cfg  # the run writes the norms through it
+        return hxc.heat2d_run(dev, u, t, cfg)[0]
+
+    def result():
+        out = np.empty_like(u0)
+        u.read_sync(out)
+        return np.concatenate([out.ravel(), hn, gn])
+    return prepare, issue, result
+
+
 def _case_host2d(dev, mode):
     """The synchronous host entry point: the field in and out of host memory,
     snapshots with host norms."""
@@ -269,6 +292,7 @@ def _case_host2d(dev, mode):
 
 
 CASES = [("heat1d", _case_heat1d, m) for m in ("plain", "graph", "fused")] + \
+        [("heat2d", _case_heat2d, m) for m in ("plain", "graph", "fused")] + \
         [("host2d", _case_host2d, m) for m in ("plain", "graph", "fused")] + \
         [("heat3d", _case_heat3d, m) for m in ("plain", "graph", "fused")] + \
         [("batch", _case_batch, m) for m in ("plain", "graph", "fused")] + \
@@ -304,3 +328,23 @@ def test_every_run_survives_an_injected_failure(dev, name, case, mode):
         assert f.wait(WAIT_NS) == hxc.HXC_OK, after
         got = result()
         assert np.array_equal(got, want), after
+
+
+def test_runs_of_every_kind_issued_together(dev):
+    """Every run entry point and mode issued back to back without waiting
+    (they share the device's streams, scratch and staging buffers), twice:
+    each result has the bits of the same run issued alone."""
+    cases = [case(dev, mode) for _, case, mode in CASES]
+    wants = []
+    for prepare, issue, result in cases:
+        prepare()
+        assert issue().wait(WAIT_NS) == hxc.HXC_OK
+        wants.append(result())
+    for rep in range(2):
+        for prepare, _, _ in cases:
+            prepare()
+        futs = [issue() for _, issue, _ in cases]
+        for f in futs:
+            assert f.wait(WAIT_NS) == hxc.HXC_OK
+        for i, ((_, _, result), want) in enumerate(zip(cases, wants)):
+            assert np.array_equal(result(), want), (rep, CASES[i][0], CASES[i][2])
