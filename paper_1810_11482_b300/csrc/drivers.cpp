@@ -10,7 +10,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <map>
+#include <mutex>
 #include <memory>
 
 #include "drivers_util.hpp"
@@ -518,6 +520,71 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
                            std::vector<FutRef> dv, FutRef *all_out, FutRef *field_out,
                            hxc_run_stats *stats_out);
 
+// A 2D run reads and replaces state the device carries from run to run (the
+// last readers of the snapshot rings, the last copy of the device norm rows)
+// while it is issued, so 2D runs on one device are issued one at a time.  A
+// run whose issue would overlap another's (another host thread, or a run
+// deferred to the worker pool) is queued and issued by the thread issuing
+// now, right after its own run; its futures complete through promises, as
+// for a deferred run.  Nobody blocks on the queue.
+struct IssueQueue {
+    std::mutex m;
+    bool busy = false;
+    std::deque<std::function<void()>> q;
+};
+
+IssueQueue &issue_queue(Device *d) {
+    static std::mutex mm;
+    static std::map<Device *, std::unique_ptr<IssueQueue>> queues;
+    std::lock_guard<std::mutex> lk(mm);
+    auto &p = queues[d];
+    if (!p) p.reset(new IssueQueue());
+    return *p;
+}
+
+// Issues the run now with `now` (its status is returned) when no other 2D
+// run is being issued on the device, else queues `later` (status OK; *all,
+// *field are promises).  `now` may be empty: `later` then serves both.
+hxc_status issue_serial(Device *d, RunIssue later, RunIssue now, FutRef *all, FutRef *field) {
+    IssueQueue &iq = issue_queue(d);
+    {
+        std::lock_guard<std::mutex> g(iq.m);
+        if (iq.busy) {
+            FutRef pa = make_pending(), pb = make_pending();
+            iq.q.push_back([pa, pb, later] {
+                FutRef ia, ib;
+                hxc_status st = later(&ia, &ib);
+                if (st) {
+                    fut_set_done(pa, st);
+                    fut_set_done(pb, st);
+                    return;
+                }
+                fut_on_done(ia, [pa](hxc_status s) { fut_set_done(pa, s); });
+                fut_on_done(ib ? ib : ia, [pb](hxc_status s) { fut_set_done(pb, s); });
+            });
+            *all = pa;
+            *field = pb;
+            return HXC_OK;
+        }
+        iq.busy = true;
+    }
+    hxc_status st = now ? now(all, field) : later(all, field);
+    for (;;) {
+        std::function<void()> next;
+        {
+            std::lock_guard<std::mutex> g(iq.m);
+            if (iq.q.empty()) {
+                iq.busy = false;
+                break;
+            }
+            next = std::move(iq.q.front());
+            iq.q.pop_front();
+        }
+        next();
+    }
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -547,16 +614,26 @@ hxc_status hxc_heat2d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, const hxc
     if (st) return st;
     if (stats_out) memset(stats_out, 0, sizeof *stats_out);
     FutRef a, b;
+    auto c = std::make_shared<hxc_heat2d_cfg>(*cfg);
     if (has_pending_host(dv)) {
-        auto c = std::make_shared<hxc_heat2d_cfg>(*cfg);
         defer_run(dv,
                   [d, u, tb, c](FutRef *ia, FutRef *ib) {
-                      return heat2d_run_impl(d, u, tb, c.get(), {}, ia, ib, nullptr);
+                      return issue_serial(d.get(), [d, u, tb, c](FutRef *ja, FutRef *jb) {
+                          return heat2d_run_impl(d, u, tb, c.get(), {}, ja, jb, nullptr);
+                      }, nullptr, ia, ib);
                   },
                   &a, &b);
     } else {
-        hxc_heat2d_cfg c = *cfg;
-        if ((st = heat2d_run_impl(d, u, tb, &c, dv, &a, &b, stats_out))) return st;
+        st = issue_serial(
+            d.get(),
+            [d, u, tb, c, dv](FutRef *ia, FutRef *ib) {
+                return heat2d_run_impl(d, u, tb, c.get(), dv, ia, ib, nullptr);
+            },
+            [&](FutRef *ia, FutRef *ib) {
+                return heat2d_run_impl(d, u, tb, c.get(), dv, ia, ib, stats_out);
+            },
+            &a, &b);
+        if (st) return st;
     }
     if (out) *out = to_handle(a);
     if (field_ready) *field_ready = to_handle(b);

@@ -348,3 +348,42 @@ def test_runs_of_every_kind_issued_together(dev):
             assert f.wait(WAIT_NS) == hxc.HXC_OK
         for i, ((_, _, result), want) in enumerate(zip(cases, wants)):
             assert np.array_equal(result(), want), (rep, CASES[i][0], CASES[i][2])
+
+
+def test_runs_issued_from_several_threads(dev):
+    """Host threads issue resident and host-memory 2D runs (with host and
+    device norms, every mode) and 3D runs at the same time, each on its own
+    buffers; every result has the bits of the same run issued alone."""
+    import threading
+    kinds = [(_case_heat2d, m) for m in ("plain", "graph", "fused")] + \
+            [(_case_host2d, "fused"), (_case_heat3d, "fused"), (_case_heat2d, "fused")]
+    cases = [case(dev, mode) for case, mode in kinds]
+    wants = []
+    for prepare, issue, result in cases:
+        prepare()
+        assert issue().wait(WAIT_NS) == hxc.HXC_OK
+        wants.append(result())
+    errors = []
+    start = threading.Barrier(len(cases))
+
+    def worker(i):
+        prepare, issue, result = cases[i]
+        try:
+            start.wait()
+            for rep in range(6):
+                prepare()
+                st = issue().wait(WAIT_NS)
+                if st != hxc.HXC_OK:
+                    errors.append((i, rep, "status %d" % st))
+                elif not np.array_equal(result(), wants[i]):
+                    errors.append((i, rep, "bits differ"))
+        except Exception as e:  # reported below, not lost in the thread
+            errors.append((i, -1, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(300)
+    assert not any(t.is_alive() for t in threads)
+    assert errors == []
