@@ -392,7 +392,12 @@ hxc_status hxc_program_release(hxc_program prog);
 /* Captures every operation subsequently issued to `dev` by this thread into
  * a CUDA graph.  Futures created during capture may be used as dependencies
  * inside the capture only.  Dependencies from before the capture must be
- * ready.  Host continuations cannot be captured (HXC_E_UNSUPPORTED). */
+ * ready.  Host continuations cannot be captured (HXC_E_UNSUPPORTED).
+ * Operations that other threads (or the worker pool) issue to `dev` during
+ * the capture wait until it ends, as does another thread's hxc_graph_begin;
+ * a wait that exceeds 60 s gives HXC_E_TIMEOUT.  So the capturing thread must
+ * not wait for another thread's operation on the same device before it ends
+ * the capture. */
 hxc_status hxc_graph_begin(hxc_device dev);
 hxc_status hxc_graph_end(hxc_device dev, hxc_graph *out);
 /* Replays the graph on slot `slot` after deps. */

@@ -190,7 +190,11 @@ hxc_status Device::scratch_get(const std::string &key, size_t bytes, void **p) {
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) return cuda_status(e, "scratch cudaMalloc");
-    e = cudaMemset(q, 0, bytes);
+    // the library's streams do not synchronize with the legacy stream, so
+    // the zero fill is waited for here: work issued after this call must
+    // not overtake it
+    e = cudaMemsetAsync(q, 0, bytes, cudaStreamLegacy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) {
         cudaFree(q);
         return cuda_status(e, "scratch cudaMemset");
@@ -498,7 +502,6 @@ void issue_deferred(std::shared_ptr<PendingOp> p) {
     DepCheck c = check_deps(p->dev.get(), p->deps, false, &waits);
     if (c == DEPS_FAILED || c == DEPS_INVALID) {
         fut_set_done(p->out, HXC_E_DEP_FAILED);
-        p->dev->deferred.fetch_sub(1);
         return;
     }
     if (c == DEPS_PENDING) {
@@ -516,22 +519,32 @@ void issue_deferred(std::shared_ptr<PendingOp> p) {
         }
     }
     issue_now(*p);
-    p->dev->deferred.fetch_sub(1);
+}
+
+// Operations from other threads wait while a thread captures a graph on the
+// device (they would otherwise land in its graph); captures are host-side
+// recordings, so the wait is short.  Called with dev->m held; false if the
+// capture did not end within the bound.
+constexpr auto kCaptureWaitBound = std::chrono::seconds(60);
+
+bool wait_foreign_capture(Device *dev, std::unique_lock<std::mutex> &lk) {
+    const auto me = std::this_thread::get_id();
+    return dev->cap_cv.wait_for(lk, kCaptureWaitBound,
+                                [dev, me] { return !dev->capturing || dev->cap_thread == me; });
 }
 
 void issue_now(PendingOp &p) {
     Device *dev = p.dev.get();
-    bool capturing, foreign;
+    bool capturing;
     {
-        std::lock_guard<std::mutex> g(dev->m);
+        std::unique_lock<std::mutex> lk(dev->m);
+        if (!wait_foreign_capture(dev, lk)) {
+            set_error("deferred operation: another thread's graph capture did not end within 60 s");
+            lk.unlock();
+            fut_set_done(p.out, HXC_E_TIMEOUT);
+            return;
+        }
         capturing = dev->capturing;
-        foreign = capturing && std::this_thread::get_id() != dev->cap_thread;
-    }
-    if (foreign) {
-        // a deferred operation became ready while another thread captures
-        set_error("deferred operation overlapped a graph capture");
-        fut_set_done(p.out, HXC_E_INVALID);
-        return;
     }
     std::vector<std::pair<cudaEvent_t, int>> waits;
     DepCheck c = check_deps(dev, p.deps, capturing, &waits);
@@ -620,12 +633,12 @@ hxc_status issue_device_op(Device *dev, int slot, const std::vector<FutRef> &dep
     }
     bool capturing;
     {
-        std::lock_guard<std::mutex> g(dev->m);
-        capturing = dev->capturing;
-        if (capturing && std::this_thread::get_id() != dev->cap_thread) {
-            set_error("device is capturing a graph on another thread");
-            return HXC_E_INVALID;
+        std::unique_lock<std::mutex> lk(dev->m);
+        if (!wait_foreign_capture(dev, lk)) {
+            set_error("another thread's graph capture did not end within 60 s");
+            return HXC_E_TIMEOUT;
         }
+        capturing = dev->capturing;
     }
     std::vector<std::pair<cudaEvent_t, int>> waits;
     DepCheck c = check_deps(dev, deps, capturing, &waits);
@@ -648,7 +661,6 @@ hxc_status issue_device_op(Device *dev, int slot, const std::vector<FutRef> &dep
             set_error("host-side dependencies cannot be captured into a graph");
             return HXC_E_UNSUPPORTED;
         }
-        dev->deferred.fetch_add(1);
         issue_deferred(p);
     } else {
         issue_now(*p);
@@ -666,20 +678,16 @@ Graph::~Graph() {
 hxc_status graph_begin(Device *dev) {
     hxc_status st = dev->make_current();
     if (st) return st;
-    // Operations deferred on host futures would be issued from a worker
-    // thread in the middle of the capture: let them drain first (bounded).
-    auto t0 = std::chrono::steady_clock::now();
-    while (dev->deferred.load() > 0) {
-        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60)) {
-            set_error("graph_begin: deferred operations did not drain within 60 s");
-            return HXC_E_TIMEOUT;
-        }
-        std::this_thread::sleep_for(std::chrono::microseconds(100));
-    }
-    std::lock_guard<std::mutex> g(dev->m);
-    if (dev->capturing) {
-        set_error("device is already capturing");
+    // operations deferred on host futures that become ready during the
+    // capture are issued by the worker pool after it (wait_foreign_capture)
+    std::unique_lock<std::mutex> g(dev->m);
+    if (dev->capturing && dev->cap_thread == std::this_thread::get_id()) {
+        set_error("this thread is already capturing a graph on the device");
         return HXC_E_INVALID;
+    }
+    if (!wait_foreign_capture(dev, g)) {
+        set_error("graph_begin: another thread's graph capture did not end within 60 s");
+        return HXC_E_TIMEOUT;
     }
     cudaError_t e = cudaSuccess;
     if (!dev->cap_origin) e = cudaStreamCreateWithFlags(&dev->cap_origin, cudaStreamNonBlocking);
@@ -730,6 +738,7 @@ hxc_status graph_end(Device *dev, Ref<Graph> *out) {
         dev->capturing = false;
         dev->cap_joined.clear();
     }
+    dev->cap_cv.notify_all();
     if (e == cudaSuccess) e = e2;
     if (failed && e == cudaSuccess) {
         set_error("an operation failed during graph capture");

@@ -108,13 +108,12 @@ struct Device : RefCounted {
     // graph capture state
     bool capturing = false;
     std::thread::id cap_thread;
+    std::condition_variable cap_cv;  // signalled when a capture ends
     cudaStream_t cap_origin = nullptr;
     cudaEvent_t cap_fork = nullptr;
     std::vector<int> cap_joined;
     std::vector<AnyRef> cap_keep;
     bool cap_failed = false;
-    // operations waiting for host futures before they can be issued
-    std::atomic<int> deferred{0};
     // scratch allocations cached by key (released with the device)
     std::unordered_map<std::string, std::pair<void *, size_t>> scratch;
     std::vector<void *> retired;  // outgrown scratch, freed with the device

@@ -343,6 +343,45 @@ def when_all(futs):
     return Future(out.value)
 
 
+class Graph:
+    """Owning wrapper of an hxc_graph handle (released on close/GC)."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def launch(self, slot=0, deps=()):
+        arr, n = _futs(deps)
+        out = c_fut()
+        check(lib().hxc_graph_launch(self.h, slot, arr, n, ctypes.byref(out)), "graph_launch")
+        return Future(out.value)
+
+    def node_count(self):
+        n = ctypes.c_size_t()
+        check(lib().hxc_graph_node_count(self.h, ctypes.byref(n)), "graph_node_count")
+        return n.value
+
+    def close(self):
+        if self.h:
+            lib().hxc_graph_release(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def graph_begin(dev):
+    check(lib().hxc_graph_begin(dev.h), "graph_begin")
+
+
+def graph_end(dev):
+    out = c_graph()
+    check(lib().hxc_graph_end(dev.h, ctypes.byref(out)), "graph_end")
+    return Graph(out.value)
+
+
 def wait_all(futs, timeout_ns=-1):
     arr, n = _futs(futs)
     return lib().hxc_wait_all(arr, n, timeout_ns)

@@ -387,3 +387,112 @@ def test_runs_issued_from_several_threads(dev):
         t.join(300)
     assert not any(t.is_alive() for t in threads)
     assert errors == []
+
+
+# ------------------------------------------------- graph capture and threads
+
+def _heat1d_chain(dev, a, b, n, steps, r=0.25, slot=0):
+    """`steps` one-step 1D launches ping-ponging between a and b (the result
+    is in a for even steps); the future of the last."""
+    f = None
+    src, dst = a, b
+    for _ in range(steps):
+        args = hxc.hxc_heat1d_args(src.h, dst.h, n, 0, n, r, 1)
+        f = dev.launch(hxc.HXC_K_HEAT1D, args, slot, deps=[f] if f is not None else ())
+        src, dst = dst, src
+    return f
+
+
+def test_graph_api_capture_and_replay(dev):
+    """hxc_graph_begin/end/launch: 20 captured 1D launches replayed three
+    times give the bits of 60 launches issued directly."""
+    n = 4099
+    u0 = synth.heat1d_input(n, seed=280)
+    a, b = dev.buffer(n * 8), dev.buffer(n * 8)
+    a.write(u0).get()
+    hxc.graph_begin(dev)
+    try:
+        _heat1d_chain(dev, a, b, n, 20)
+    finally:
+        g = hxc.graph_end(dev)
+    assert g.node_count() >= 20
+    f = None
+    for _ in range(3):
+        f = g.launch(0, deps=[f] if f is not None else ())
+    assert f.wait(WAIT_NS) == hxc.HXC_OK
+    got = np.empty(n)
+    a.read_sync(got)
+    c, d = dev.buffer(n * 8), dev.buffer(n * 8)
+    c.write(u0).get()
+    assert _heat1d_chain(dev, c, d, n, 60).wait(WAIT_NS) == hxc.HXC_OK
+    want = np.empty(n)
+    c.read_sync(want)
+    assert np.array_equal(got, want)
+    assert np.max(np.abs(got - oracle.heat1d(u0, 0.25, 60))) <= 1e-12 * np.max(np.abs(u0))
+    g.close()
+
+
+def test_capture_holds_other_threads_operations(dev):
+    """While one thread captures a graph, operations that another thread and
+    the worker pool issue to the device wait for the capture to end instead
+    of landing in the graph (or failing): they run afterwards with the right
+    results, and the graph holds only the capturing thread's launches."""
+    import threading
+    import time
+    n = 2048
+    u0 = synth.heat1d_input(n, seed=281)
+    a, b = dev.buffer(n * 8), dev.buffer(n * 8)
+    c, d = dev.buffer(n * 8), dev.buffer(n * 8)
+    e, f_ = dev.buffer(n * 8), dev.buffer(n * 8)
+    a.write(u0).get()
+    e.write(u0).get()
+    hxc.graph_begin(dev)  # the same capture alone, for its node count
+    try:
+        _heat1d_chain(dev, a, b, n, 10)
+    finally:
+        solo = hxc.graph_end(dev)
+    gate = hxc.promise()
+    # a launch deferred on a host promise, set while the capture runs
+    deferred = dev.launch(hxc.HXC_K_HEAT1D, hxc.hxc_heat1d_args(e.h, f_.h, n, 0, n, 0.25, 1), 3,
+                          deps=[gate])
+    capturing, res = threading.Event(), {}
+
+    def capturer():
+        hxc.graph_begin(dev)
+        try:
+            capturing.set()
+            _heat1d_chain(dev, a, b, n, 10)
+            hxc.promise_set(gate, hxc.HXC_OK)
+            time.sleep(0.3)
+            res["t_end"] = time.perf_counter()
+        finally:
+            res["graph"] = hxc.graph_end(dev)
+
+    def other():
+        capturing.wait(30)
+        c.write(u0).get()
+        res["t_other"] = time.perf_counter()
+        res["other"] = _heat1d_chain(dev, c, d, n, 10, slot=5).wait(WAIT_NS)
+
+    ts = [threading.Thread(target=capturer), threading.Thread(target=other)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(120)
+    assert not any(t.is_alive() for t in ts)
+    assert res["t_other"] >= res["t_end"]
+    assert res["other"] == hxc.HXC_OK
+    assert deferred.wait(WAIT_NS) == hxc.HXC_OK
+    g = res["graph"]
+    assert g.node_count() == solo.node_count() >= 10
+    solo.close()
+    assert g.launch(0).wait(WAIT_NS) == hxc.HXC_OK
+    want = oracle.heat1d(u0, 0.25, 10)
+    for buf in (a, c):
+        got = np.empty(n)
+        buf.read_sync(got)
+        assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(u0))
+    got = np.empty(n)
+    f_.read_sync(got)
+    assert np.max(np.abs(got - oracle.heat1d(u0, 0.25, 1))) <= 1e-12 * np.max(np.abs(u0))
+    g.close()
