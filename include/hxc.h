@@ -460,7 +460,11 @@ typedef struct {
  * as u holds the result, possibly before the host norms finish.  The cfg
  * struct is copied; the norm arrays must stay valid until *out is ready.
  * When a dependency is unfinished host work the whole run is issued later
- * by the worker pool (stats then count nothing). */
+ * by the worker pool (stats then count nothing).  2D runs on one device are
+ * issued one at a time (they share the device's snapshot rings and norm
+ * rows): a run called while another thread issues one is queued and issued
+ * by that thread right after, without blocking the caller (stats again
+ * count nothing; errors then reach *out instead of the return value). */
 hxc_status hxc_heat2d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, const hxc_heat2d_cfg *cfg,
                           const hxc_future *deps, int ndeps, hxc_future *out,
                           hxc_future *field_ready, hxc_run_stats *stats);
