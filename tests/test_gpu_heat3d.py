@@ -157,6 +157,15 @@ def test_heat3d_full_size_windows(dev):
     assert got.max() <= u0.max() + 1e-6 and got.min() >= u0.min() - 1e-6
     ref, _ = run3d(dev, u0, 200, "graph", 4)
     assert np.array_equal(got, ref)
+    # every two-plane form gives these bits at full size too
+    old = hxc.tune_get("heat3d.variant")
+    try:
+        for variant in (3, 4):
+            hxc.tune_set("heat3d.variant", variant)
+            other, _ = run3d(dev, u0, 200, "fused", 4)
+            assert np.array_equal(other, got), variant
+    finally:
+        hxc.tune_set("heat3d.variant", old)
 
 
 def test_heat3d_product_mode_full_size(dev):
