@@ -443,6 +443,12 @@ def secondary(dev, timer, peaks):
                        "traffic": traffic3,
                        "kernel": "k_heat3d_v4<4> (4 steps of the whole 512^3 field per launch)",
                        "effective_gbs_1step_equiv": 2 * u3.nbytes * st3 / (res["fused"]["ms"] / 1e3) / 1e9}
+    # the one-step launches of plain mode (streaming kernel): read + write once per step
+    ms1 = res["plain"]["ms"] / st3
+    gbs1 = 2 * u3.nbytes / (ms1 / 1e3) / 1e9
+    res["roofline_one_step"] = {"bound": "hbm", "achieved": gbs1, "peak": peaks["hbm_gbs"],
+                                "unit": "GB/s", "frac": gbs1 / peaks["hbm_gbs"], "ms_per_launch": ms1,
+                                "kernel": "k_heat3d_s1 (one step of the whole 512^3 field per launch)"}
     out["heat3d_512^3_200steps_f32"] = res
     del u3
 

@@ -600,8 +600,10 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *                  (default).  Forms 3 and 4 launched with an hxc_launch_cfg
  *                  take 512 threads per CTA and any grid.
  *   "heat3d.variant1"  the form used for one-step launches (PLAIN mode and
- *                  single-step remainders), same values (default 0: with a
- *                  single level the copied-plane form is the fastest).
+ *                  single-step remainders), the values above plus 5 = a
+ *                  streaming kernel (4 adjacent x cells per thread, 16-byte
+ *                  loads, 64-plane z chunks; nx % 4 == 0 and 16-byte aligned
+ *                  fields without a launch cfg, else form 3), the default.
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
  *   "mandel.pair"  Mandelbrot kernel form: 1 = two horizontally adjacent

@@ -107,7 +107,7 @@ def tune(quick=False, log=print):
     result.update(best3)
     # one-step launches (PLAIN mode) choose their form separately
     run31 = lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 8, "plain", 1, d)[0]
-    result.update(_search(timer, {"heat3d.variant1": [0, 1, 2, 3, 4]}, run31, log))
+    result.update(_search(timer, {"heat3d.variant1": [0, 1, 2, 3, 4, 5]}, run31, log))
     del a, b
     # 1D: CTAs per partition of the temporally blocked kernel
     n1 = 1 << 20

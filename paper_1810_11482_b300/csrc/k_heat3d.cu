@@ -835,6 +835,90 @@ int heat3d_blocks(int nz, int ny, int nx, int T, int zchunk) {
     return ((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * ((nz + zchunk - 1) / zchunk);
 }
 
+// ---------------------------------------------------------------------------
+// Form 5, one step per launch: a streaming kernel.  A thread owns 4 adjacent
+// x cells of one row (16-byte loads and stores; nx % 4 == 0) and walks a
+// chunk of S1_ZC planes with the planes z-1, z and z+1 of its cells in
+// registers.  The x neighbours beyond its 4 cells come from the adjacent
+// lanes by shuffles (a lane at the warp's or the field's x end loads its
+// own, wrapped), the y neighbours are 16-byte loads of the rows above and
+// below (wrapped), which the warps holding those rows load as their own, so
+// they are mostly L1 and L2 hits.  Arithmetic on paired FP32 instructions in
+// the canonical order.  Grid: (nx / 128 rounded up, ny / S1_ROWS rounded up,
+// nz / S1_ZC rounded up) CTAs of 32 x S1_ROWS threads.
+namespace {
+constexpr int S1_ROWS = 8, S1_ZC = 64;
+
+__device__ __forceinline__ ulonglong2 ld16(const float *p) {
+    return __ldg(reinterpret_cast<const ulonglong2 *>(p));
+}
+}  // namespace
+
+__global__ void __launch_bounds__(32 * S1_ROWS) k_heat3d_s1(const float *__restrict__ src,
+                                                           float *__restrict__ dst, int nz, int ny,
+                                                           int nx, float r) {
+    const int lane = threadIdx.x & 31;
+    const int x = (blockIdx.x * 32 + lane) * 4;
+    const int y = blockIdx.y * S1_ROWS + (threadIdx.x >> 5);
+    const int z0 = blockIdx.z * S1_ZC, z1 = min(nz, z0 + S1_ZC);
+    const bool active = x < nx && y < ny;
+    const int yy = active ? y : 0, xx = active ? x : 0;
+    const int ym = yy == 0 ? ny - 1 : yy - 1, yp = yy + 1 == ny ? 0 : yy + 1;
+    const size_t plane = (size_t)ny * nx;
+    const size_t oc = (size_t)yy * nx + xx, om = (size_t)ym * nx + xx, op = (size_t)yp * nx + xx;
+    // x neighbours: shuffled from the adjacent lane when it holds them, else loaded
+    const bool own_l = lane == 0, own_r = lane == 31 || x + 4 >= nx;
+    const size_t ol = (size_t)yy * nx + (xx == 0 ? nx - 1 : xx - 1);
+    const size_t orr = (size_t)yy * nx + (xx + 4 >= nx ? 0 : xx + 4);
+    const f2 r2 = pk(r, r), m6 = pk(-6.0f, -6.0f);
+    auto wz = [nz](int z) { return z >= nz ? z - nz : (z < 0 ? z + nz : z); };
+    // planes z-1, z, z+1 of the thread's cells, the rows above and below and
+    // the loaded x neighbours of plane z; every load is issued one plane ahead
+    ulonglong2 zm = {0ull, 0ull}, u = {0ull, 0ull}, zp = {0ull, 0ull}, a = {0ull, 0ull},
+               b = {0ull, 0ull};
+    float xl = 0.0f, xr = 0.0f;
+    if (active) {
+        const float *pz = src + plane * (size_t)z0;
+        zm = ld16(src + plane * (size_t)wz(z0 - 1) + oc);
+        u = ld16(pz + oc);
+        zp = ld16(src + plane * (size_t)wz(z0 + 1) + oc);
+        a = ld16(pz + om);
+        b = ld16(pz + op);
+        if (own_l) xl = __ldg(pz + ol);
+        if (own_r) xr = __ldg(pz + orr);
+    }
+    for (int z = z0; z < z1; z++) {
+        ulonglong2 pre = {0ull, 0ull}, na = {0ull, 0ull}, nb = {0ull, 0ull};
+        float nxl = 0.0f, nxr = 0.0f;
+        if (active && z + 1 < z1) {
+            const float *pn = src + plane * (size_t)wz(z + 1);
+            pre = ld16(src + plane * (size_t)wz(z + 2) + oc);
+            na = ld16(pn + om);
+            nb = ld16(pn + op);
+            if (own_l) nxl = __ldg(pn + ol);
+            if (own_r) nxr = __ldg(pn + orr);
+        }
+        const float sl = __shfl_up_sync(0xffffffffu, hi_of(u.y), 1);
+        const float sr = __shfl_down_sync(0xffffffffu, lo_of(u.x), 1);
+        // cells (c0, c1) = u.x, (c2, c3) = u.y
+        const f2 xmA = pk(own_l ? xl : sl, lo_of(u.x)), xpA = pk(hi_of(u.x), lo_of(u.y));
+        const f2 xpB = pk(hi_of(u.y), own_r ? xr : sr);
+        const f2 sA = add2(add2(add2(add2(xmA, xpA), add2(a.x, b.x)), zm.x), zp.x);
+        const f2 sB = add2(add2(add2(add2(xpA, xpB), add2(a.y, b.y)), zm.y), zp.y);
+        ulonglong2 o;
+        o.x = fma2(r2, fma2(m6, u.x, sA), u.x);
+        o.y = fma2(r2, fma2(m6, u.y, sB), u.y);
+        if (active) *reinterpret_cast<ulonglong2 *>(dst + plane * (size_t)z + oc) = o;
+        zm = u;
+        u = zp;
+        zp = pre;
+        a = na;
+        b = nb;
+        xl = nxl;
+        xr = nxr;
+    }
+}
+
 // z chunk length: split z so that the CTA count fills whole waves of one
 // CTA per SM (each extra chunk re-reads 3T-1 planes).
 int heat3d_default_zchunk(int nz, int ny, int nx, int T) {
@@ -869,6 +953,14 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
     // one-step launches have a knob of their own: with a single level the
     // copied-plane form streams faster than the two-plane forms
     const int64_t variant = tune::get(steps == 1 ? "heat3d.variant1" : "heat3d.variant");
+    if (variant == 5 && steps == 1 && !cfg && nx % 4 == 0 && (ny + S1_ROWS - 1) / S1_ROWS <= 65535 &&
+        (nz + S1_ZC - 1) / S1_ZC <= 65535 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+        dim3 grid((unsigned)((nx + 127) / 128), (unsigned)((ny + S1_ROWS - 1) / S1_ROWS),
+                  (unsigned)((nz + S1_ZC - 1) / S1_ZC));
+        k_heat3d_s1<<<grid, 32 * S1_ROWS, 0, s>>>(src, dst, nz, ny, nx, r);
+        return cudaGetLastError();
+    }
     if (variant >= 3 && (uint64_t)ny * (uint64_t)nx <= 0xffffffffull) {
         if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != V3_NW * 32)
             return cudaErrorInvalidValue;

@@ -30,7 +30,7 @@ Knob g_knobs[] = {
     {"heat2d.occupancy", 4, 4, 6},    // compiled minimum of CTAs per SM
     {"heat3d.zchunks", 0, 0, 64},     // z chunks per launch (0: fill whole waves)
     {"heat3d.variant", 4, 0, 4},      // 0 copied, 1 rotated, 2 rotated + f32x2, 3 two-plane, 4 + ring
-    {"heat3d.variant1", 0, 0, 4},     // the same choice for one-step launches
+    {"heat3d.variant1", 5, 0, 5},     // the same choice for one-step launches, 5 = streaming one-step kernel
     {"heat1d.tb_ctas", 0, 0, 1 << 16},  // CTAs per partition of the 1D blocked kernel (0: SMs/parts)
     {"mandel.pair", 1, 0, 1},         // Mandelbrot: 1 = two pixels per thread on paired FP32
     {"batch.ctas_per_sm", 4, 1, 16},  // CTAs per SM of the persistent batch kernel

@@ -2,6 +2,7 @@
 
     python -m paper_1810_11482_b300.profile_cases heat2d [n] [launches]
     python -m paper_1810_11482_b300.profile_cases heat3d [nz ny nx] [steps]
+    python -m paper_1810_11482_b300.profile_cases heat3d_step [nz ny nx] [steps]
     python -m paper_1810_11482_b300.profile_cases batch [nprob] [steps]
     python -m paper_1810_11482_b300.profile_cases adjoint [n] [steps]
     python -m paper_1810_11482_b300.profile_cases partition [n] [parts]
@@ -35,6 +36,17 @@ def heat3d(nz=256, ny=512, nx=512, steps=8):
     u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
     u.write(u0).get()
     f, st = hxc.heat3d_run(dev, u, t, (nz, ny, nx), 0.15, steps, "fused", 4)
+    f.get()
+    return st.kernel_launches
+
+
+def heat3d_step(nz=512, ny=512, nx=512, steps=4):
+    """One step per launch (PLAIN mode): the one-step kernel form."""
+    dev = hxc.get_all_devices(2, 0)[0]
+    u0 = synth.uniform(6, nz * ny * nx).astype(np.float32)
+    u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    u.write(u0).get()
+    f, st = hxc.heat3d_run(dev, u, t, (nz, ny, nx), 0.15, steps, "plain", 1)
     f.get()
     return st.kernel_launches
 
@@ -81,7 +93,8 @@ def mandelbrot(side=4096, max_iter=256):
     return 1
 
 
-CASES = {"heat2d": heat2d, "heat3d": heat3d, "batch": batch, "adjoint": adjoint,
+CASES = {"heat2d": heat2d, "heat3d": heat3d, "heat3d_step": heat3d_step, "batch": batch,
+         "adjoint": adjoint,
          "partition": partition, "mandelbrot": mandelbrot}
 
 if __name__ == "__main__":

@@ -122,6 +122,28 @@ def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
             hxc.tune_set(k, v)
 
 
+@pytest.mark.parametrize("shape", [(40, 72, 96), (70, 33, 132), (8, 8, 8), (130, 17, 4),
+                                   (3, 5, 128), (9, 70, 131)])
+def test_heat3d_streaming_one_step_form(dev, shape):
+    """The streaming one-step kernel (one-step form 5): z chunks with a ragged
+    last chunk, rows not filling the last CTA, a partial last warp in x, tiny
+    and degenerate shapes, and an odd nx (which takes another form) give the
+    bits of the copied-plane form, step after step."""
+    u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=360 + shape[0], nz=shape[0],
+                                                 ny=shape[1]), dtype=np.float32)
+    old = hxc.tune_get("heat3d.variant1")
+    try:
+        hxc.tune_set("heat3d.variant1", 0)
+        ref, _ = run3d(dev, u0, 7, "plain", 1)
+        hxc.tune_set("heat3d.variant1", 5)
+        for mode in ("plain", "graph", "fused"):
+            got, _ = run3d(dev, u0, 7, mode, 1)
+            assert np.array_equal(got, ref), mode
+    finally:
+        hxc.tune_set("heat3d.variant1", old)
+    assert relerr(ref, oracle.heat3d(u0.astype(np.float64), float(R), 7)) <= TOL32
+
+
 def test_heat3d_medium_vs_oracle_200_steps(dev):
     u0 = synth.heat3d_input(64, seed=320)
     want = oracle.heat3d(u0.astype(np.float64), float(R), 200)
