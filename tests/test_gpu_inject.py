@@ -291,6 +291,62 @@ def _case_host2d(dev, mode):
     return prepare, issue, result
 
 
+def _case_mandelbrot(dev, mode):
+    """An image computed, copied back and written as a PNG file, the write
+    synchronous ("plain") or a continuation ("fused"); the result is the
+    file's bytes."""
+    import tempfile
+    w, h = 257, 123
+    path = tempfile.mkdtemp(prefix="hxc_inject_") + "/m.png"
+    rgb = dev.buffer(w * h * 3)
+    host = np.zeros(w * h * 3, dtype=np.uint8)
+    args = hxc.mandelbrot_args(rgb, w, h, -2.0, -1.2, 3.0 / w, 2.4 / h, 200)
+
+    def prepare():
+        host[:] = 0
+
+    def issue():
+        issue.rgb = rgb  # the argument block holds its handle only
+        return hxc.mandelbrot_png(dev, args, host, path, level=1, async_write=(mode == "fused"))
+
+    def result():
+        with open(path, "rb") as fh:
+            return np.frombuffer(fh.read(), dtype=np.uint8).copy()
+    return prepare, issue, result
+
+
+PROG_SRC = r"""
+extern "C" __global__ void axpb(double *x, double a, double b, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = a * x[i] + b;
+}
+"""
+
+
+def _case_program(dev, mode):
+    """A run-time compiled kernel (the paper's program.run) on a buffer."""
+    import ctypes
+    n = 10007
+    x0 = np.linspace(-1.0, 1.0, n)
+    buf = dev.buffer(n * 8)
+    prog = hxc.Program.from_source(dev, PROG_SRC, "axpb.cu")
+    assert prog.build("axpb").wait(WAIT_NS) == hxc.HXC_OK, prog.log()
+
+    def prepare():
+        buf.write(x0).get()
+
+    def issue():
+        issue.prog = prog  # kept alive with the case
+        return prog.run("axpb", [buf, ctypes.c_double(0.5), ctypes.c_double(0.25),
+                                 ctypes.c_longlong(n)], ((n + 255) // 256, 1, 1), (256, 1, 1))
+
+    def result():
+        out = np.empty(n)
+        buf.read_sync(out)
+        return out
+    return prepare, issue, result
+
+
 CASES = [("heat1d", _case_heat1d, m) for m in ("plain", "graph", "fused")] + \
         [("heat2d", _case_heat2d, m) for m in ("plain", "graph", "fused")] + \
         [("host2d", _case_host2d, m) for m in ("plain", "graph", "fused")] + \
@@ -298,7 +354,9 @@ CASES = [("heat1d", _case_heat1d, m) for m in ("plain", "graph", "fused")] + \
         [("batch", _case_batch, m) for m in ("plain", "graph", "fused")] + \
         [("adjoint", _case_adjoint, m) for m in ("plain", "graph", "fused")] + \
         [("forward", _case_forward, "fused"), ("stream2d", _case_stream2d, "plain"),
-         ("stream2d", _case_stream2d, "fused"), ("partition", _case_partition, "fused")]
+         ("stream2d", _case_stream2d, "fused"), ("partition", _case_partition, "fused"),
+         ("mandelbrot", _case_mandelbrot, "plain"), ("mandelbrot", _case_mandelbrot, "fused"),
+         ("program", _case_program, "plain")]
 
 
 @pytest.mark.parametrize("name,case,mode", CASES, ids=["%s-%s" % (c[0], c[2]) for c in CASES])
