@@ -302,6 +302,22 @@ def test_heat2d_full_config(dev):
                                    .astype(np.longdouble) ** 2))
                     for i in range(8) for j in range(8)], dtype=np.float64)
     assert np.max(np.abs(hn[-1] - fin) / fin) <= 1e-13
+    # the end-to-end form the benchmark times: the field from pinned host
+    # memory through the asynchronous host entry point, two calls in flight
+    hu = hxc.host_empty((n, n))
+    hu[:] = u0
+    outs_h, keep = [], []
+    for _ in range(2):
+        ho = hxc.host_empty((n, n))
+        hn2, gn2 = np.zeros(10 * 64), np.zeros(10 * 64)
+        cfg = hxc.heat2d_cfg(n, n, 8, 8, r, steps, every, "fused", hn2, gn2)
+        f, _ = hxc.heat2d_run_host_async(dev, hu.ctypes.data, ho.ctypes.data, cfg)
+        outs_h.append((f, ho, hn2, gn2))
+        keep.append(cfg)
+    for f, ho, hn2, gn2 in outs_h:
+        assert f.wait(600 * 10**9) == hxc.HXC_OK
+        assert np.array_equal(np.array(ho), got)
+        assert np.array_equal(hn2, hn.ravel()) and np.array_equal(gn2, gn.ravel())
 
 
 def test_heat2d_full_size_window_at_peak(dev):
