@@ -366,7 +366,8 @@ hxc_status issue_steps2d(Heat2dRun &R, int64_t s0, int64_t s1, std::vector<FutRe
 // Issues the device part of snapshot k (taken after step `step`): the tile
 // snapshot + device norm kernels into ring slot k % 2.
 hxc_status issue_snap_kernels(Heat2dRun &R, int64_t k, int64_t step, std::vector<FutRef> &prev,
-                              const std::vector<FutRef> &ring_free, bool fused) {
+                              const std::vector<FutRef> &ring_free, bool fused,
+                              const FutRef &norm_free = FutRef()) {
     const hxc_heat2d_cfg &c = *R.cfg;
     const int64_t T = R.tl.count();
     const double *src = R.buf[step % 2];
@@ -380,6 +381,7 @@ hxc_status issue_snap_kernels(Heat2dRun &R, int64_t k, int64_t step, std::vector
             }
         for (auto &f : ring_free)
             if (f) deps.push_back(f);
+        if (norm_free) deps.push_back(norm_free);
         void *scratch = nullptr;
         hxc_status st = R.dev->scratch_get("tile_norm_grid", k::tile_norm_grid_scratch_bytes(T), &scratch);
         if (st) return st;
@@ -402,6 +404,7 @@ hxc_status issue_snap_kernels(Heat2dRun &R, int64_t k, int64_t step, std::vector
         std::vector<FutRef> deps;
         if (prev[t]) deps.push_back(prev[t]);
         if (ring_free.size() > (size_t)t && ring_free[t]) deps.push_back(ring_free[t]);
+        if (norm_free) deps.push_back(norm_free);
         double *snap = c.host_norms ? R.snap_dev + ((k % 2) * T + t) * R.tile_stride : nullptr;
         double *norms = R.norm_dev;
         int64_t idx = k * T + t;
@@ -721,12 +724,14 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             return st;
     }
 
-    // the device norm rows are shared by the runs on this device: this run
-    // writes them only after the last run's rows have been copied out
-    if (cfg->gpu_norms && want_snaps) {
+    // the device norm rows are shared by the runs on this device: this run's
+    // first snapshot writes them only after the last run's rows have been
+    // copied out (its steps need not wait)
+    FutRef norm_free;
+    if (want_snaps) {
         GnormStage &gs = gnorm_stage(d.get());
         std::lock_guard<std::mutex> lk(gs.m);
-        if (FutRef c = fut_order_only(gs.copied)) dv.push_back(c);
+        norm_free = fut_order_only(gs.copied);
     }
     Ref<RunResources> res(new RunResources(), true);
     res->keep = {AnyRef(u.get(), false), AnyRef(tb.get(), false)};
@@ -805,6 +810,7 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
                 if (p) gdeps.push_back(p);
             for (auto &f : ring_free[ring])
                 if (f) gdeps.push_back(f);
+            if (k == 0 && norm_free) gdeps.push_back(norm_free);
             // dedupe: the same future may appear for every tile
             std::vector<FutRef> uniq;
             for (auto &f : gdeps) {
@@ -836,7 +842,8 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             }
         } else {
             if ((st = issue_steps2d(R, s, s1, prev, fused))) return st;
-            if (snap_here && (st = issue_snap_kernels(R, k, s1, prev, ring_free[ring], fused)))
+            if (snap_here && (st = issue_snap_kernels(R, k, s1, prev, ring_free[ring], fused,
+                                                      k == 0 ? norm_free : FutRef())))
                 return st;
         }
         if (snap_here) {
