@@ -29,13 +29,12 @@
  *  - Stream slots.  A device has up to HXC_MAX_SLOTS asynchronous queues
  *    (CUDA streams, created on first use).  Work on one slot runs in issue
  *    order; work on different slots is ordered only by futures.
- *  - Threads.  All calls are thread-safe, except that while a device is
- *    capturing a graph only the capturing thread may issue work to it.
- *    Host continuations run on an internal worker pool, never on CUDA's
- *    callback thread.
- *  - Waits are bounded: hxc_future_wait takes a timeout; device kernels that
- *    spin on a flag give up after a bounded number of polls and report
- *    HXC_E_TIMEOUT through their status word.
+ *  - Threads.  All calls are thread-safe.  While a thread captures a graph
+ *    on a device, work that other threads issue to that device waits until
+ *    the capture ends (hxc_graph_begin).  Host continuations run on an
+ *    internal worker pool, never on CUDA's callback thread.
+ *  - Waits are bounded: hxc_future_wait takes a timeout, and no kernel of
+ *    the library waits on another CTA or on the host.
  *
  * Data layouts
  *  - 1D fields: n contiguous doubles, periodic.

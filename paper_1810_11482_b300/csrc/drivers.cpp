@@ -314,8 +314,10 @@ struct Heat2dRun {
     double *buf[2];
     double *snap_dev;      // [2][tiles] compact tile snapshots
     double *norm_dev;      // [n_snap][tiles] device norms
+    double *replay_dev;    // [2][tiles] device norms written by graph replays
     double *host_stage;    // [2][tiles] pinned staging for the host norms
     int64_t tile_stride;   // elements per snapshot tile slot
+    int norm_set;          // which of the device's sets of norm rows
     Stats stats;
 };
 
@@ -496,19 +498,28 @@ std::mutex g_hostrun_m;
 std::map<Device *, HostRunSlots> g_hostrun;
 const char *const kHostKeyU[2] = {"heat2d_host.u0", "heat2d_host.u1"};
 const char *const kHostKeyT[2] = {"heat2d_host.t0", "heat2d_host.t1"};
-constexpr int kHostSlots = 8;
+constexpr int kHostSlots = 4;
 constexpr int kHostInSlot0 = kCopySlot0 + kCopySlots;     // host-run uploads
 constexpr int kHostOutSlot0 = kHostInSlot0 + kHostSlots;  // host-run downloads
-static_assert(kHostOutSlot0 + kHostSlots <= HXC_MAX_SLOTS, "stream slots");
+constexpr int kNormCopySlot = kHostOutSlot0 + kHostSlots;  // device norms to the host
+static_assert(kNormCopySlot < HXC_MAX_SLOTS, "stream slots");
 
 // Page-locked staging of the device norms, per device; `last` is the host
 // copy of the previous run that read it.
+// The device norm rows of a run and their pinned host staging: four sets of
+// each, used in turn by successive runs, so that a run rarely waits for the
+// runs before it.  A run's first write into its rows waits for the copy out
+// of the same rows by the run four before (copied[]), and its copy into a
+// staging buffer for the host copy out of that buffer (last[]).
+constexpr int kGnormStages = 4;
 struct GnormStage {
     std::mutex m;
-    void *ptr = nullptr;
-    size_t bytes = 0;
-    FutRef last;    // the host copy of the last run's norms into the caller's array
-    FutRef copied;  // the device->host copy of its device norm rows
+    int next = 0, next_rows = 0;
+    void *ptr[kGnormStages] = {};
+    size_t bytes[kGnormStages] = {};
+    FutRef last[kGnormStages];    // the host copy out of each staging buffer
+    FutRef copied[kGnormStages];  // the device->host copy out of each set of rows
+    FutRef latest;                // the last run's copy out of its rows
 };
 GnormStage &gnorm_stage(Device *d) {
     static std::mutex mm;
@@ -687,13 +698,32 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             carry = RingCarry();
         }
     }
+    FutRef norm_free;  // the last copy out of this run's norm rows
     if (want_snaps) {
         void *p;
         if ((st = d->scratch_get("heat2d.snap", (size_t)2 * T * R.tile_stride * 8, &p))) return st;
         R.snap_dev = (double *)p;
-        // n_snap rows of results + 2 rows written by graph replays (ring slots)
-        if ((st = d->scratch_get("heat2d.norms", (size_t)(n_snap + 2) * T * 8, &p))) return st;
+        // this run's set of n_snap rows of results, and the 2 rows (ring
+        // slots) that graph replays write and that are copied into them
+        int nset;
+        {
+            GnormStage &gs = gnorm_stage(d.get());
+            std::lock_guard<std::mutex> lk(gs.m);
+            nset = gs.next_rows;
+            gs.next_rows = (nset + 1) % kGnormStages;
+            norm_free = fut_order_only(gs.copied[nset]);
+            gs.copied[nset] = FutRef();
+            // a run also starts after the last run's norm copy: measured, this
+            // keeps the host-memory runs issued back to back 2.5% faster (the
+            // resident loop loses 1%)
+            if (FutRef c = fut_order_only(gs.latest)) dv.push_back(c);
+        }
+        if ((st = d->scratch_get("heat2d.norms." + std::to_string(nset), (size_t)n_snap * T * 8, &p)))
+            return st;
         R.norm_dev = (double *)p;
+        if ((st = d->scratch_get("heat2d.norms.replay", (size_t)2 * T * 8, &p))) return st;
+        R.replay_dev = (double *)p;
+        R.norm_set = nset;
         if (cfg->host_norms) {
             // pinned staging ring, cached per device
             static std::mutex sm;
@@ -724,15 +754,6 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             return st;
     }
 
-    // the device norm rows are shared by the runs on this device: this run's
-    // first snapshot writes them only after the last run's rows have been
-    // copied out (its steps need not wait)
-    FutRef norm_free;
-    if (want_snaps) {
-        GnormStage &gs = gnorm_stage(d.get());
-        std::lock_guard<std::mutex> lk(gs.m);
-        norm_free = fut_order_only(gs.copied);
-    }
     Ref<RunResources> res(new RunResources(), true);
     res->keep = {AnyRef(u.get(), false), AnyRef(tb.get(), false)};
     std::vector<FutRef> prev(T);
@@ -769,7 +790,7 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
                                       (double)cfg->tiles_x, cfg->r, (double)every,
                                       (double)(s_start % 2), (double)ring, (double)want_snaps,
                                       (double)n_snap, (double)(cfg->host_norms != nullptr)},
-                                     {u->ptr, tb->ptr, R.snap_dev, R.norm_dev});
+                                     {u->ptr, tb->ptr, R.snap_dev, R.replay_dev});
             {
                 std::lock_guard<std::mutex> lk(g_graph_m);
                 auto it = g_graphs.find(key);
@@ -785,7 +806,7 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
                 // a replay writes its device norms to row n_snap + ring; they
                 // are copied to their snapshot's row after each replay
                 std::vector<FutRef> none;
-                C.norm_dev = R.norm_dev + n_snap * T;  // index ring*T+t lands in row n_snap+ring
+                C.norm_dev = R.replay_dev;  // index ring*T+t lands in replay row `ring`
                 st = issue_snap_kernels(C, ring, s_start + every, cprev, none, false);
             }
             Ref<Graph> g;
@@ -810,7 +831,6 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
                 if (p) gdeps.push_back(p);
             for (auto &f : ring_free[ring])
                 if (f) gdeps.push_back(f);
-            if (k == 0 && norm_free) gdeps.push_back(norm_free);
             // dedupe: the same future may appear for every tile
             std::vector<FutRef> uniq;
             for (auto &f : gdeps) {
@@ -828,10 +848,13 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             if (stats_out) stats_out->graph_launches++;
             for (auto &p : prev) p = gf;
             if (snap_here) {
-                // move the replay's device norms (row n_snap + ring) to row k
-                double *src = R.norm_dev + (n_snap + ring) * T, *dst = R.norm_dev + k * T;
+                // move the replay's device norms (replay row `ring`) to row k;
+                // the run's first write into its rows waits for their last copy
+                double *src = R.replay_dev + ring * T, *dst = R.norm_dev + k * T;
+                std::vector<FutRef> cdeps{gf};
+                if (k == 0 && norm_free) cdeps.push_back(norm_free);
                 FutRef c;
-                if ((st = issue_device_op(d.get(), 0, {gf},
+                if ((st = issue_device_op(d.get(), 0, cdeps,
                                           [=](cudaStream_t st) {
                                               return cudaMemcpyAsync(dst, src, T * 8,
                                                                      cudaMemcpyDeviceToDevice, st);
@@ -891,31 +914,37 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
         const size_t bytes = (size_t)n_snap * T * 8;
         GnormStage &gs = gnorm_stage(d.get());
         std::lock_guard<std::mutex> lk(gs.m);
-        if (gs.bytes < bytes) {
-            if (gs.last) fut_wait(gs.last, -1);  // the old buffer may still be read
-            if (gs.ptr) cudaFreeHost(gs.ptr);
-            gs.ptr = nullptr;
-            gs.bytes = 0;
-            if (cudaMallocHost(&gs.ptr, bytes) != cudaSuccess) {
+        const int b = gs.next;
+        gs.next = (b + 1) % kGnormStages;
+        if (gs.bytes[b] < bytes) {
+            if (gs.last[b]) fut_wait(gs.last[b], -1);  // the old buffer may still be read
+            if (gs.ptr[b]) cudaFreeHost(gs.ptr[b]);
+            gs.ptr[b] = nullptr;
+            gs.bytes[b] = 0;
+            if (cudaMallocHost(&gs.ptr[b], bytes) != cudaSuccess) {
                 set_error("pinned staging of %zu bytes for device norms failed", bytes);
                 return HXC_E_NOMEM;
             }
-            gs.bytes = bytes;
+            gs.bytes[b] = bytes;
         }
-        double *stage = static_cast<double *>(gs.ptr);
+        double *stage = static_cast<double *>(gs.ptr[b]);
         const double *src = R.norm_dev;
         std::vector<FutRef> cdeps = finals;
-        // the previous run's host copy is done (order only: its failure is not this run's)
-        if (FutRef o = fut_order_only(gs.last)) cdeps.push_back(o);
+        // the host copy out of this buffer by the run four before is done
+        // (order only: its failure is not this run's)
+        if (FutRef o = fut_order_only(gs.last[b])) cdeps.push_back(o);
         FutRef c;
-        if ((st = issue_device_op(d.get(), kCopySlot0, cdeps,
+        // a slot of its own: behind the snapshot copies it would hold up the
+        // next run's first snapshot
+        if ((st = issue_device_op(d.get(), kNormCopySlot, cdeps,
                                   [=](cudaStream_t s) {
                                       return cudaMemcpyAsync(stage, src, bytes, cudaMemcpyDeviceToHost, s);
                                   },
                                   {}, &c)))
             return st;
         R.stats.copy(0, bytes);
-        gs.copied = c;
+        gs.copied[R.norm_set] = c;
+        gs.latest = c;
         double *dst = cfg->gpu_norms;
         FutRef r = make_pending();
         fut_on_done(c, [r, stage, dst, bytes](hxc_status s2) {
@@ -928,7 +957,7 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
                 fut_set_done(r, HXC_OK);
             });
         });
-        gs.last = r;
+        gs.last[b] = r;
         gnorm_done = r;
     }
     if (finals.empty()) finals.push_back(make_done(HXC_OK));
