@@ -504,13 +504,12 @@ constexpr int kHostOutSlot0 = kHostInSlot0 + kHostSlots;  // host-run downloads
 constexpr int kNormCopySlot = kHostOutSlot0 + kHostSlots;  // device norms to the host
 static_assert(kNormCopySlot < HXC_MAX_SLOTS, "stream slots");
 
-// Page-locked staging of the device norms, per device; `last` is the host
-// copy of the previous run that read it.
 // The device norm rows of a run and their pinned host staging: four sets of
-// each, used in turn by successive runs, so that a run rarely waits for the
-// runs before it.  A run's first write into its rows waits for the copy out
-// of the same rows by the run four before (copied[]), and its copy into a
-// staging buffer for the host copy out of that buffer (last[]).
+// each, used in turn by successive runs.  A run's first write into its rows
+// waits for the copy out of the same rows by the run four before (copied[]),
+// its copy into a staging buffer for the host copy out of that buffer by the
+// run four before (last[]), and the run as a whole starts after the previous
+// run's copy of its rows (latest).
 constexpr int kGnormStages = 4;
 struct GnormStage {
     std::mutex m;
