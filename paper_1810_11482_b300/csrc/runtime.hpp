@@ -126,7 +126,8 @@ struct Device : RefCounted {
     void put_event(cudaEvent_t e);
     // Device memory cached under `key`, at least `bytes` large, zero-filled
     // when first allocated.  Valid until the device is destroyed, also after
-    // a larger request for the same key has replaced it.
+    // a larger request for the same key has replaced it (devices live until
+    // the process ends).
     hxc_status scratch_get(const std::string &key, size_t bytes, void **p);
 };
 
