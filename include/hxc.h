@@ -483,9 +483,10 @@ hxc_status hxc_heat2d_run_host(hxc_device dev, const double *host_u0, double *ho
  * overlap.  Calls whose snapshot norms go to the same arrays must not
  * overlap (each run writes every entry).  The two field pairs grow to the
  * largest field used; a pair outgrown by a larger call stays allocated (an
- * operation still to be issued may hold it) until the process ends.  Argument errors are returned
- * synchronously with no future created; a failure of a copy or of the run
- * is stored in *out and does not affect later calls. */
+ * operation still to be issued may hold it) until the process ends.
+ * Argument errors are returned synchronously with no future created; a
+ * failure of a copy or of the run is stored in *out and does not affect
+ * later calls. */
 hxc_status hxc_heat2d_run_host_async(hxc_device dev, const double *host_u0, double *host_uT,
                                      const hxc_heat2d_cfg *cfg, const hxc_future *deps,
                                      int ndeps, hxc_future *out, hxc_run_stats *stats);
