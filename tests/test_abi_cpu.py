@@ -266,3 +266,21 @@ def test_debug_inject_arguments():
     assert L.hxc_debug_inject(ctypes.c_int64(5), hxc.HXC_E_CUDA) == hxc.HXC_OK
     assert L.hxc_debug_inject(ctypes.c_int64(-1), hxc.HXC_OK) == hxc.HXC_OK
     hxc.debug_inject(-1)
+
+
+def test_host_run_and_graph_calls_reject_bad_arguments(L):
+    """Argument checks of the host-memory run entry points and the graph
+    calls come before any device work, so they hold without a GPU."""
+    bogus = ctypes.c_void_p(0)
+    cfg = hxc.heat2d_cfg(64, 64, 2, 2, 0.2, 4, 2, "fused", None, None)
+    host = np.zeros((64, 64))
+    out = hxc.c_fut()
+    st = hxc.hxc_run_stats()
+    assert L.hxc_heat2d_run_host_async(bogus, host.ctypes.data, host.ctypes.data, ctypes.byref(cfg),
+                                       None, 0, ctypes.byref(out), ctypes.byref(st)) == hxc.HXC_E_INVALID
+    assert L.hxc_heat2d_run_host(bogus, host.ctypes.data, host.ctypes.data, ctypes.byref(cfg),
+                                 ctypes.byref(st)) == hxc.HXC_E_INVALID
+    assert L.hxc_graph_begin(bogus) == hxc.HXC_E_INVALID
+    g = hxc.c_graph()
+    assert L.hxc_graph_end(bogus, ctypes.byref(g)) == hxc.HXC_E_INVALID
+    assert L.hxc_graph_launch(bogus, 0, None, 0, ctypes.byref(out)) == hxc.HXC_E_INVALID
