@@ -16,24 +16,51 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64 = ctypes.c_int64
 
 
 def build():
-    """Compile liboracle.so with -O2 -ffp-contract=off (no FMA contraction)."""
-    subprocess.check_call(["make", "-s", "-C", _HERE, "liboracle.so"])
+    """Compile liboracle.so with -O2 -ffp-contract=off (no FMA contraction),
+    and liboracle_omp.so, the same source with OpenMP enabled."""
+    subprocess.check_call(["make", "-s", "-C", _HERE, "all"])
+
+
+def _stale(path):
+    src = os.path.join(_HERE, "oracle.c")
+    return not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(src)
+
+
+def _declare_steps(L):
+    L.ora_heat2d_steps.argtypes = [_dp, _dp, _i64, _i64, ctypes.c_double, ctypes.c_int]
+    L.ora_heat2d_steps.restype = ctypes.c_void_p
+    L.ora_threads.restype = ctypes.c_int
+
+
+def lib_omp():
+    """The OpenMP build (liboracle_omp.so): only the row loop of the 2D
+    stepping routine differs, and only in running on all threads."""
+    global _lib_omp
+    if _lib_omp is None:
+        if _stale(_LIB_OMP):
+            build()
+        L = ctypes.CDLL(_LIB_OMP)
+        _declare_steps(L)
+        _lib_omp = L
+    return _lib_omp
 
 
 def lib():
     global _lib
     if _lib is None:
-        src = os.path.join(_HERE, "oracle.c")
-        if not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(src):
+        if _stale(_LIB):
             build()
         L = ctypes.CDLL(_LIB)
+        _declare_steps(L)
         L.ora_prk_stencil.argtypes = [_dp, _dp, _i64]
         L.ora_sum_u32.argtypes = [ctypes.POINTER(ctypes.c_uint32), _i64]
         L.ora_sum_u32.restype = ctypes.c_uint64
@@ -128,6 +155,22 @@ def heat2d(u0, r, steps):
     out = np.empty_like(u0)
     lib().ora_heat2d(_p(u0), _p(out), u0.shape[0], u0.shape[1], r, steps)
     return out
+
+
+def heat2d_steps(a, b, r, steps, omp=False):
+    """2D FTCS as heat2d, stepping the caller's C-contiguous float64 arrays in
+    place (a holds u^0, b is scratch; no allocation or copy inside).  Returns
+    whichever of a, b holds u^steps.  omp=True runs the OpenMP build."""
+    assert a.dtype == np.float64 and b.dtype == np.float64 and a.shape == b.shape
+    assert a.flags.c_contiguous and b.flags.c_contiguous
+    L = lib_omp() if omp else lib()
+    res = L.ora_heat2d_steps(_p(a), _p(b), a.shape[0], a.shape[1], r, steps)
+    return a if res == a.ctypes.data else b
+
+
+def threads(omp=False):
+    """Threads the 2D stepping routine runs on (1 for the serial build)."""
+    return int((lib_omp() if omp else lib()).ora_threads())
 
 
 def heat2d_window(u0, wy0, wx0, wny, wnx, r, steps):

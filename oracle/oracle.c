@@ -37,6 +37,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef int64_t i64;
 
@@ -82,13 +85,18 @@ static double at2(const double *u, i64 ny, i64 nx, i64 i, i64 j) {
 }
 
 /* 2D FTCS, 5-point Laplacian, Dirichlet-zero ghosts:
- * u' = u + r (u_W + u_E + u_S + u_N - 4u).  Row-major, index (i, j) = (y, x). */
-void ora_heat2d(const double *u0, double *out, i64 ny, i64 nx, double r, int steps) {
-    i64 n = ny * nx;
-    double *a = (double *)malloc(sizeof(double) * n);
-    double *b = (double *)malloc(sizeof(double) * n);
-    memcpy(a, u0, sizeof(double) * n);
+ * u' = u + r (u_W + u_E + u_S + u_N - 4u).  Row-major, index (i, j) = (y, x).
+ * Steps caller-owned ping-pong arrays: a holds u^0 on entry, b is scratch;
+ * returns the array that holds u^steps (a for an even count, else b).
+ * Within a step every cell reads only the previous state, so the rows are
+ * independent: the OpenMP build of this file (liboracle_omp.so) runs the
+ * row loop on all threads, the serial build runs it in order, and both
+ * perform exactly the same operations on every cell. */
+double *ora_heat2d_steps(double *a, double *b, i64 ny, i64 nx, double r, int steps) {
     for (int t = 0; t < steps; t++) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (i64 i = 0; i < ny; i++)
             for (i64 j = 0; j < nx; j++) {
                 double c = a[i * nx + j];
@@ -99,8 +107,28 @@ void ora_heat2d(const double *u0, double *out, i64 ny, i64 nx, double r, int ste
             }
         double *tmp = a; a = b; b = tmp;
     }
-    memcpy(out, a, sizeof(double) * n);
+    return a;
+}
+
+/* The same run on a copy: out = u^steps from u0 (u0 is not modified). */
+void ora_heat2d(const double *u0, double *out, i64 ny, i64 nx, double r, int steps) {
+    i64 n = ny * nx;
+    double *a = (double *)malloc(sizeof(double) * n);
+    double *b = (double *)malloc(sizeof(double) * n);
+    memcpy(a, u0, sizeof(double) * n);
+    double *res = ora_heat2d_steps(a, b, ny, nx, r, steps);
+    memcpy(out, res, sizeof(double) * n);
     free(a); free(b);
+}
+
+/* Number of threads the row loop of ora_heat2d_steps uses (1 in the serial
+ * build). */
+int ora_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* 2D FTCS restricted to a window of a larger domain.  The window

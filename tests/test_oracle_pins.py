@@ -181,6 +181,22 @@ def test_heat2d_window_matches_full():
     assert np.array_equal(w[:-steps, :-steps], full[:20 - steps, :20 - steps])
 
 
+@pytest.mark.parametrize("ny,nx,steps", [(1, 1, 3), (3, 500, 5), (257, 130, 6), (600, 77, 1)])
+def test_heat2d_stepping_builds_agree(ny, nx, steps):
+    """The caller-buffer stepping routine equals heat2d, and its OpenMP build
+    (rows on all threads) equals the serial build bit for bit, on ragged
+    shapes with odd and even step counts (the result may end in either
+    array)."""
+    u0 = synth.uniform(77 + nx, ny * nx, lo=-1.0, hi=1.0).reshape(ny, nx)
+    want = oracle.heat2d(u0, 0.2, steps)
+    for omp in (False, True):
+        a, b = u0.copy(), np.full_like(u0, np.nan)
+        got = oracle.heat2d_steps(a, b, 0.2, steps, omp=omp)
+        assert got is (a if steps % 2 == 0 else b)
+        assert np.array_equal(got, want), omp
+    assert oracle.threads(False) == 1 and oracle.threads(True) >= 1
+
+
 def test_heat2d_max_principle():
     u0 = synth.bumps2d(40, 40, seed=34, nbumps=3, sigma=0.1)
     ut = oracle.heat2d(u0, 0.25, 100)
