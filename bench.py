@@ -47,6 +47,14 @@ OPS_PER_UPDATE_2D = 4
 BYTES_PER_UPDATE_2D = 16  # one 8-byte read and one 8-byte write
 
 
+def bench_config(world):
+    """The workload as both arms name it."""
+    return {"workload": "heat2d FTCS 8192x8192 FP64, 64 tiles of 1024^2, r=0.2, "
+                        "1000 steps, snapshot+host L2 norms every 100 steps",
+            "parallelism": "replicas x%d" % world,
+            "l2": "field 2x512 MiB > 126 MB L2 (no flush needed)"}
+
+
 def load_peaks():
     p = os.path.join(HERE, "MEASURED_PEAKS.json")
     peaks = {"hbm_gbs": 6400.0, "hbm_source": "fallback", "sm_max_mhz": 2032.0, "sms": 148}
@@ -55,9 +63,38 @@ def load_peaks():
         peaks["hbm_gbs"] = float(d.get("hbm_gbs", 6400.0))
         peaks["hbm_source"] = "measured"
         peaks["sm_max_mhz"] = float(d.get("sm_max_mhz", 2032.0))
-    # FP64 pipe: 2 operations (DADD / DMUL / DFMA) per clock per SM on B300
-    peaks["fp64_gops"] = 2 * peaks["sms"] * peaks["sm_max_mhz"] / 1e3
+    # nominal FP64 pipe: 2 operations (DADD / DMUL / DFMA) per clock per SM on
+    # B300; replaced by the measured rate when a device is at hand
+    peaks["fp64_nominal_gops"] = 2 * peaks["sms"] * peaks["sm_max_mhz"] / 1e3
+    peaks["fp64_gops"] = peaks["fp64_nominal_gops"]
+    peaks["fp64_source"] = "nominal: 2 ops/clk/SM x 148 SMs x %.0f MHz" % peaks["sm_max_mhz"]
+    peaks["fp32_nominal_gops"] = 128 * peaks["sms"] * peaks["sm_max_mhz"] / 1e3
+    peaks["fp32_gops"] = peaks["fp32_nominal_gops"]
+    peaks["fp32_source"] = "nominal: 128 ops/clk/SM x 148 SMs x %.0f MHz" % peaks["sm_max_mhz"]
     return peaks
+
+
+def measure_pipes(dev, peaks):
+    """The FP64 and FP32 pipe rates measured on this device now
+    (hxc_pipe_rate: chains of one instruction, CUDA-event timed), which
+    become the peaks of the arithmetic-bound rooflines."""
+    from paper_1810_11482_b300 import hxc
+    res = {}
+    for name, kind in (("f64_fma", hxc.HXC_PIPE_F64_FMA), ("f64_add", hxc.HXC_PIPE_F64_ADD),
+                       ("f32_fma", hxc.HXC_PIPE_F32_FMA)):
+        ops, mhz = hxc.pipe_rate(dev, kind)
+        res[name] = {"gops": ops / 1e9, "sm_mhz": mhz,
+                     "per_sm_clock": ops / (dev.sm_count * mhz * 1e6) if mhz > 0 else None}
+    peaks["fp64_gops"] = res["f64_fma"]["gops"]
+    peaks["fp64_source"] = ("measured here: FP64 FMA stream (hxc_pipe_rate) at %.0f MHz; "
+                            "nominal %.1f Gop/s" % (res["f64_fma"]["sm_mhz"],
+                                                    peaks["fp64_nominal_gops"]))
+    peaks["fp32_gops"] = res["f32_fma"]["gops"]
+    peaks["fp32_source"] = ("measured here: FP32 FMA stream (hxc_pipe_rate) at %.0f MHz; "
+                            "nominal %.1f Gop/s" % (res["f32_fma"]["sm_mhz"],
+                                                    peaks["fp32_nominal_gops"]))
+    peaks["pipes"] = res
+    return res
 
 
 class Clocks:
@@ -192,6 +229,7 @@ def ours(args, world, rank, local, pg):
         raise RuntimeError("no CUDA device visible")
     dev = devs[local % len(devs)]
     peaks = load_peaks()
+    measure_pipes(dev, peaks)
     T = TILES[0] * TILES[1]
     nsnap = STEPS2D // EVERY
     u0 = synth.bumps2d(NY, NX, seed=2)
@@ -305,7 +343,8 @@ def ours(args, world, rank, local, pg):
             "frac": ach_gops / peaks["fp64_gops"], "traffic": traffic,
             "kernel": "k_heat2d<2> (whole 8192^2 field, one step per launch, 4 FP64 ops/update)",
             "ms_per_launch": kms,
-            "peak_source": "FP64 pipe: 2 ops/clk/SM x 148 SMs x %.0f MHz" % peaks["sm_max_mhz"],
+            "peak_source": peaks["fp64_source"], "nominal_peak": peaks["fp64_nominal_gops"],
+            "frac_of_nominal": ach_gops / peaks["fp64_nominal_gops"],
             "hbm": {"achieved_gbs": ach_gbs, "peak_gbs": peaks["hbm_gbs"],
                     "frac": ach_gbs / peaks["hbm_gbs"], "peak_source": peaks["hbm_source"]}}
 
@@ -367,21 +406,46 @@ def ours(args, world, rank, local, pg):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "heat2d FTCS 8192x8192 FP64, 64 tiles of 1024^2, r=0.2, "
-                               "1000 steps, snapshot+host L2 norms every 100 steps",
-                   "mode": best_mode, "parallelism": "replicas x%d" % world,
-                   "l2": "field 2x512 MiB > 126 MB L2 (no flush needed)"},
+        "config": bench_config(world), "launch_mode": best_mode,
         "roofline": roof, "gpu_launches": int(allsum(pg, n_launch)), "modes": modes,
         "clocks": clk, "e2e": e2e, "paper_protocol": protocol, "overlap": overlap,
-        "secondary": sec,
+        "pipe_peaks": peaks.get("pipes"), "secondary": sec,
     }
+    if sec:
+        out["secondary_summary"] = summarize(sec)
+    return out
+
+
+def summarize(sec):
+    """The secondary workloads' key figures in a few numbers (kept at the end
+    of the line, where a truncated log still shows them)."""
+    r = lambda x: None if x is None else float("%.4g" % x)
+    out = {}
+    h1 = sec.get("heat1d_2^20_8parts_100steps_f64")
+    if h1:
+        out["heat1d_ms"] = {m: r(h1[m]["ms"]) for m in ("plain", "graph", "fused")}
+    h3 = sec.get("heat3d_512^3_200steps_f32")
+    if h3:
+        out["heat3d_ms"] = {m: r(h3[m]["ms"]) for m in ("plain", "graph", "fused")}
+        out["heat3d_4step_launch"] = {"ms": r(h3["roofline"]["ms_per_launch"]),
+                                      "hbm_frac": r(h3["roofline"]["frac"])}
+        out["heat3d_1step_launch_hbm_frac"] = r(h3["roofline_one_step"]["frac"])
+    b = sec.get("batch_4096_problems_50steps_f64")
+    if b:
+        out["batch_ms"] = {m: r(b[m]["ms"]) for m in ("plain", "graph", "fused")}
+        out["batch_fp64_frac"] = r(b["roofline"]["frac"])
+    a = sec.get("adjoint_2048^2_500steps_f64")
+    if a:
+        out["adjoint_ms"] = {m: r(a[m]["ms"]) for m in ("forward", "plain", "graph", "fused")}
+        out["gradient_over_forward"] = r(a["gradient_over_forward_time"])
+        out["adjoint_fused_speedup_vs_plain"] = r(a["fused"]["speedup_vs_plain"])
     return out
 
 
 def fp64_roof(ops, ms, peaks, what):
     ach = ops / (ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": ach, "peak": peaks["fp64_gops"], "unit": "Gop/s",
-            "frac": ach / peaks["fp64_gops"], "count": what}
+            "frac": ach / peaks["fp64_gops"], "count": what, "peak_source": peaks["fp64_source"]}
 
 
 def secondary(dev, timer, peaks):
@@ -506,11 +570,8 @@ def secondary(dev, timer, peaks):
     del b0, bkr, bkk, tgt, uT, lam, lb, gk, gu
     out["heat2d_streamed_8192_64tiles_f64"] = stream2d_bench(dev)
     out["partition_alg1_p4_f64"] = partition_bench(dev, timer)
-    out["mandelbrot_png_f32"] = mandelbrot_bench(dev, timer)
+    out["mandelbrot_png_f32"] = mandelbrot_bench(dev, timer, peaks)
     return out
-
-
-FP32_LANES_PER_SM = 128  # FP32 operations per SM per clock (an FMA counts as one)
 
 
 def mandelbrot_frames(n, frames, max_iter):
@@ -528,7 +589,8 @@ def mandelbrot_frames(n, frames, max_iter):
     return out
 
 
-def mandelbrot_bench(dev, timer, sides=(1024, 2048, 4096, 8192), frames=8, max_iter=256, level=1):
+def mandelbrot_bench(dev, timer, peaks, sides=(1024, 2048, 4096, 8192), frames=8, max_iter=256,
+                     level=1):
     """Sec. 5.1.3: for each image size, a sequence of `frames` images (a zoom)
     computed on the device, copied back and written as PNG files (zlib
     level 1); host-clock time of the sequence with each file written
@@ -579,11 +641,12 @@ def mandelbrot_bench(dev, timer, sides=(1024, 2048, 4096, 8192), frames=8, max_i
         kms = float(np.median(kms[1:]))
         # 7 FP32 operations per full iteration, 3 for the final escape test
         ops = 7.0 * counts.astype(np.float64).sum() + 3.0 * float((counts < max_iter).sum())
-        peak = 148 * FP32_LANES_PER_SM * 2032e6 / 1e9
+        peak = peaks["fp32_gops"]
         res["kernel"] = {"side": n, "ms": kms, "iterations": float(counts.astype(np.float64).sum()),
                          "roofline": {"bound": "alu", "achieved": ops / (kms / 1e3) / 1e9,
                                       "peak": peak, "unit": "Gop/s (FP32)",
-                                      "frac": ops / (kms / 1e3) / 1e9 / peak}}
+                                      "frac": ops / (kms / 1e3) / 1e9 / peak,
+                                      "peak_source": peaks["fp32_source"]}}
         return res
     finally:
         shutil.rmtree(tmp, ignore_errors=True)
@@ -693,42 +756,105 @@ def partition_bench(dev, timer, ms_exp=range(1, 9), parts=4):
                                         "device->host copied concurrently on two streams"}}
 
 
-def cpu_baseline(sample_steps=3):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    headline workload: the full 8192^2 field advanced `sample_steps` steps."""
-    import oracle
-    from paper_1810_11482_b300 import synth
-    u0 = synth.bumps2d(NY, NX, seed=2)
-    oracle.heat2d(u0[:64, :64], R2D, 1)  # load/compile
-    t0 = time.perf_counter()
-    oracle.heat2d(u0, R2D, sample_steps)
-    el = time.perf_counter() - t0
-    return {"value": NY * NX * sample_steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "full 8192^2 field, %d of the 1000 steps (single-threaded C, -O2, no FMA)"
-                      % sample_steps, "seconds": el}
+def cpu_info():
+    """Host CPU model and the number of logical CPUs this process may use."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"cpu_model": model, "nproc": usable, "cpu_count": os.cpu_count()}
+
+
+class OracleRun:
+    """The oracle's 2D FTCS stepping routine on the headline field, stepping
+    two caller-owned arrays (both touched before any timing, so no allocation,
+    copy or page fault is inside a timed call).  omp=True is the OpenMP build
+    of the same loop (all host threads), omp=False the serial build."""
+
+    def __init__(self, omp):
+        import oracle
+        from paper_1810_11482_b300 import synth
+        self.oracle = oracle
+        self.omp = omp
+        self.a = synth.bumps2d(NY, NX, seed=2)
+        self.b = np.zeros_like(self.a)
+        self.threads = oracle.threads(omp)
+
+    def run(self, steps):
+        """Advances the field `steps` time steps in one call; seconds taken."""
+        t0 = time.perf_counter()
+        res = self.oracle.heat2d_steps(self.a, self.b, R2D, steps, omp=self.omp)
+        el = time.perf_counter() - t0
+        if res is self.b:
+            self.a, self.b = self.b, self.a
+        return el
+
+    def steps_for(self, seconds, cap):
+        """Time steps per call that take about `seconds` (one calibration step)."""
+        t1 = self.run(1)
+        return max(1, min(cap, int(round(seconds / max(t1, 1e-6)))))
+
+
+def oracle_protocol(warmup, steps):
+    """The oracle (OpenMP build, all host threads) timed on the headline
+    workload: each bench step advances the full 8192^2 field `k` = 10 time
+    steps in one call (0.2-0.3 s on an 8-core host), continuing the evolution; `warmup`
+    untimed bench steps, then the mean of `steps` timed ones.  The serial
+    build is timed once beside it.  The field's far tails pass through
+    subnormal values, which the host's FP64 unit handles slowly, so the rate
+    depends on the stretch of the evolution sampled: the benchmark's CPU
+    baseline and its reference arm therefore take the same stretch."""
+    info = cpu_info()
+    o = OracleRun(True)
+    k = 10
+    times = []
+    for i in range(warmup + steps):
+        el = o.run(k)
+        if i >= warmup:
+            times.append(el)
+    per = statistics.mean(times)
+    threads = o.threads
+    del o
+    st = OracleRun(False)
+    ks = st.steps_for(2.0, 20)
+    el_s = st.run(ks)
+    return {"value": NY * NX * k / per, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "full 8192^2 field from u0, %d + %d bench steps of %d time steps each "
+                      "(one call each, continuing the evolution), OpenMP build (row loop on %d "
+                      "threads; C, -O2, no FMA)" % (warmup, steps, k, threads),
+            "seconds_per_step": per, "time_steps_per_step": k,
+            "single_thread": {"value": NY * NX * ks / el_s, "cores": 1,
+                              "sample": "full field from u0, %d time steps in one call" % ks},
+            **info}
+
+
+def cpu_baseline(warmup, steps):
+    """The oracle as it stands on the host cores, on the same bounded sample
+    as the reference arm (oracle_protocol)."""
+    return oracle_protocol(warmup, steps)
 
 
 def reference(args, world, rank):
+    """The reference arm: the oracle on the headline workload
+    (oracle_protocol); under torchrun rank 0 alone runs it."""
     if rank != 0:
         return None
-    steps = []
-    base = None
-    for i in range(args.warmup + args.steps):
-        b = cpu_baseline(1)
-        if i >= args.warmup:
-            steps.append(b["seconds"])
-        base = b
-    per = statistics.mean(steps)
-    value = NY * NX / per
-    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+    b = oracle_protocol(args.warmup, args.steps)
+    value = b["value"]
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": b["seconds_per_step"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "heat2d FTCS 8192x8192 FP64, 64 tiles of 1024^2, r=0.2, "
-                                   "1000 steps, snapshot+host L2 norms every 100 steps",
-                       "sample": "each step: the full field advanced 1 time step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "full 8192^2 field, 1 time step per bench step"},
+            "data": "synthetic", "config": bench_config(world), "cpu_baseline": b,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -755,7 +881,9 @@ def main():
     out = ours(args, world, rank, local, pg)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(args.warmup, args.steps)
+        if "secondary_summary" in out:  # keep it last
+            out["secondary_summary"] = out.pop("secondary_summary")
         print(json.dumps(out), flush=True)
     if pg is not None:
         pg.destroy_process_group()
