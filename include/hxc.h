@@ -624,6 +624,26 @@ hxc_status hxc_tune_get(const char *key, int64_t *value);
  * the library, automatically. */
 hxc_status hxc_tune_load(const char *path, int major, int minor);
 
+/* ------------------------------------------------------- diagnostics */
+
+/* Arithmetic pipes hxc_pipe_rate can measure. */
+#define HXC_PIPE_F64_FMA 0 /* FP64 fused multiply-add */
+#define HXC_PIPE_F64_ADD 1 /* FP64 add                */
+#define HXC_PIPE_F32_FMA 2 /* FP32 fused multiply-add */
+
+/* The paper has no counterpart to this call.  Measured throughput of one
+ * arithmetic pipe of the device, the denominator of the rooflines of
+ * arithmetic-bound kernels (the FP64 stencils here are bound by the FP64
+ * pipe, not by memory).  A kernel of independent dependency chains that
+ * issues only the measured instruction (8 chains per thread, 8 CTAs of 256
+ * threads per SM) runs once to warm up and once timed with CUDA events
+ * (about 0.1 s on B300).  *ops_per_s: operations per second, a fused
+ * multiply-add counting as one; *sm_mhz (may be NULL): the SM clock during
+ * the timed launch, from the first CTA's clock64 ticks over globaltimer
+ * nanoseconds.  Synchronous; allocates and frees a few MB of device memory
+ * and a private stream.  HXC_E_INVALID for an unknown kind. */
+hxc_status hxc_pipe_rate(hxc_device dev, int kind, double *ops_per_s, double *sm_mhz);
+
 /* ------------------------------------------- norms without allocation */
 
 /* Largest tile grid (tiles_y * tiles_x) hxc_tile_norms_noalloc accepts. */
@@ -640,16 +660,18 @@ hxc_status hxc_tune_load(const char *path, int major, int minor);
  * device memory: a time-critical loop in which cudaMalloc would synchronise
  * the device, a process whose device memory belongs to another allocator,
  * or a deployment that forbids allocation after start-up.  Its reduction
- * scratch is a fixed array of about 129 KB compiled into the library and
+ * scratch is a fixed array of about 132 KB compiled into the library and
  * held on every GPU that loads it until the process exits; grids of more
  * than HXC_NOALLOC_MAX_TILES tiles are rejected with HXC_E_INVALID.
  *
  * src and norms are device pointers on the current device, stream a
  * cudaStream_t (NULL: the legacy default stream); the call is asynchronous
- * on that stream and returns launch errors only.  The first call on a device
- * looks up the scratch array's device address (cudaGetSymbolAddress) with
- * that device current: make it before any stream capture.  Every call on a
- * device shares the one array and clears the counters it needs; calls whose
+ * on that stream and returns launch errors only.  Every call looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with the current
+ * device, so the address follows device switches and device resets; the
+ * first call in a process may load the library's device code for that
+ * device, so make it before any stream capture.  Every call on a device
+ * shares the one array and clears the counters it needs; calls whose
  * executions overlap on the GPU (different streams, no ordering) race on
  * it and must be serialised by the caller. */
 hxc_status hxc_tile_norms_noalloc(const double *src, int64_t ny, int64_t nx, int64_t tiles_y,

@@ -39,6 +39,10 @@ HXC_K_ADJOINT2D = 8
 HXC_K_PARTITION = 9
 HXC_K_MANDELBROT = 10
 
+HXC_PIPE_F64_FMA = 0
+HXC_PIPE_F64_ADD = 1
+HXC_PIPE_F32_FMA = 2
+
 HXC_MODE_PLAIN = 0
 HXC_MODE_GRAPH = 1
 HXC_MODE_FUSED = 2
@@ -243,6 +247,8 @@ _SIGS = {
     "hxc_tune_load": (c_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int]),
     "hxc_tile_norms_noalloc": (c_st, [ctypes.c_void_p, i64, i64, i64, i64, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    "hxc_pipe_rate": (c_st, [c_dev, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)]),
     "hxc_heat2d_run_host": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.POINTER(hxc_heat2d_cfg), ctypes.POINTER(hxc_run_stats)]),
     "hxc_heat2d_run_host_async": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
@@ -636,6 +642,14 @@ def host_empty(shape, dtype=np.float64):
     if isinstance(shape, int):
         shape = (shape,)
     return np.asarray(_Pinned(shape, np.dtype(dtype)))
+
+
+def pipe_rate(dev, kind):
+    """Measured throughput of one arithmetic pipe (HXC_PIPE_*): (operations
+    per second, SM clock in MHz during the measurement)."""
+    ops, mhz = ctypes.c_double(), ctypes.c_double()
+    check(lib().hxc_pipe_rate(dev.h, kind, ctypes.byref(ops), ctypes.byref(mhz)), "pipe_rate")
+    return ops.value, mhz.value
 
 
 def tune_set(key, value):
