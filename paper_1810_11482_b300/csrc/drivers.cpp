@@ -283,27 +283,37 @@ struct HostNormTask {
     double *out;
 };
 
-// sqrt(sum v^2) of a snapshot tile on the host: blocks of 1024 squares are
-// summed with 8 independent accumulators (vectorisable), the block sums
-// pairwise; for these non-negative terms the relative error stays below
-// about (1024/8 + log2(blocks) + 2) * 2^-53 ~ 2e-14.
+// sqrt(sum v^2) of a snapshot tile on the host, accumulated in long double
+// (x87 extended precision, unit roundoff u = 2^-64): blocks of 1024 squares
+// are summed with 8 independent accumulators, the block sums pairwise.  The
+// squares of doubles and these sums of non-negative terms carry a relative
+// error below (1024/8 + 3 + log2(blocks) + 1) u ~ 8e-18 for a 1024^2 tile, so
+// the result is the exact norm correctly rounded to double within about
+// one part in 1e16 (the tolerance asked of the host norms against a
+// long-double reference sum is 1e-14).
 hxc_status host_norm_fn(void *user) {
     HostNormTask *t = static_cast<HostNormTask *>(user);
     const double *x = t->data;
     const int64_t n = t->count, B = 1024;
-    std::vector<double> blocks((n + B - 1) / B);
+    std::vector<long double> blocks((n + B - 1) / B);
     for (int64_t b0 = 0, k = 0; b0 < n; b0 += B, k++) {
         const int64_t e = std::min(n, b0 + B);
-        double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        long double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int64_t i = b0;
         for (; i + 8 <= e; i += 8)
-            for (int q = 0; q < 8; q++) a[q] += x[i + q] * x[i + q];
-        for (; i < e; i++) a[0] += x[i] * x[i];
+            for (int q = 0; q < 8; q++) {
+                const long double v = x[i + q];
+                a[q] += v * v;
+            }
+        for (; i < e; i++) {
+            const long double v = x[i];
+            a[0] += v * v;
+        }
         blocks[k] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     }
     for (size_t w = 1; w < blocks.size(); w *= 2)
         for (size_t k = 0; k + w < blocks.size(); k += 2 * w) blocks[k] += blocks[k + w];
-    *t->out = blocks.empty() ? 0.0 : std::sqrt(blocks[0]);
+    *t->out = blocks.empty() ? 0.0 : (double)std::sqrt(blocks[0]);
     return HXC_OK;
 }
 
