@@ -155,13 +155,22 @@ def adjoint_input(n=2048, seeds=(5, 6, 7), c=0.15):
     return kref, kap, u0, c
 
 
-def fd_directions(ndir, n_kappa, n_u0, seed=8):
-    """`ndir` Gaussian directions over the joint (dkappa, du0), each normalised
-    to unit 2-norm.  Returns (dk [ndir, n_kappa], du [ndir, n_u0])."""
+def fd_direction(k, n_kappa, n_u0, seed=8):
+    """Direction k (k = 0, 1, ...) of the finite-difference check: a Gaussian
+    vector over the joint (dkappa, du0), drawn from position k (n_kappa + n_u0)
+    of the stream and normalised to unit 2-norm, so that one full-size
+    direction at a time can be generated.  Returns (dk, du)."""
     m = n_kappa + n_u0
-    d = normal(seed, ndir * m).reshape(ndir, m)
-    d /= np.linalg.norm(d, axis=1, keepdims=True)
-    return d[:, :n_kappa], d[:, n_kappa:]
+    d = normal(seed, m, start=k * m)
+    d /= np.linalg.norm(d)
+    return d[:n_kappa], d[n_kappa:]
+
+
+def fd_directions(ndir, n_kappa, n_u0, seed=8):
+    """Directions 0 .. ndir-1 of fd_direction stacked.
+    Returns (dk [ndir, n_kappa], du [ndir, n_u0])."""
+    rows = [fd_direction(k, n_kappa, n_u0, seed) for k in range(ndir)]
+    return np.stack([r[0] for r in rows]), np.stack([r[1] for r in rows])
 
 
 def partition_sizes(ms=range(1, 9), block=256, parts=4):
