@@ -421,8 +421,9 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
     if (every == 0) every = std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, steps))));
     const int nseg = steps > 0 ? (steps + every - 1) / every : 0;
     // scratch: coefficients, checkpoints 1..nseg-1, the segment store
-    // (states 1..every-1 of a segment), two work fields, two adjoint fields
-    void *pe, *ps, *pm, *pck, *pseg, *pw, *pl;
+    // (states 1..every-1 of a segment), two work fields, two adjoint fields,
+    // the per-face gradient sums
+    void *pe, *ps, *pm, *pck, *pseg, *pw, *pl, *pf;
     if ((st = dev->scratch_get("adj.wE", nb, &pe))) return st;
     if ((st = dev->scratch_get("adj.wS", nb, &ps))) return st;
     if ((st = dev->scratch_get("adj.m", nb, &pm))) return st;
@@ -430,8 +431,11 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
     if ((st = dev->scratch_get("adj.seg", nb * std::max(1, every), &pseg))) return st;
     if ((st = dev->scratch_get("adj.work", nb * 2, &pw))) return st;
     if ((st = dev->scratch_get("adj.lam", nb * 2, &pl))) return st;
+    const size_t face_bytes = k::vc_face_doubles(ny, nx) * 8;
+    if ((st = dev->scratch_get("adj.face", face_bytes, &pf))) return st;
     double *WE = (double *)pe, *WS = (double *)ps, *M = (double *)pm;
     double *CK = (double *)pck, *SEG = (double *)pseg, *WK = (double *)pw, *LM = (double *)pl;
+    double *FACE = (double *)pf;
     const double *U0 = (const double *)u0->ptr, *K = (const double *)kap->ptr,
                  *LT = (const double *)lT->ptr;
     double *GK = (double *)gk->ptr, *GU = (double *)gu0->ptr, *UT = uT ? (double *)uT->ptr : nullptr;
@@ -467,10 +471,10 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
             sc.launch();
             cur = dst;
         }
-        // adjoint seed and gradient accumulator
+        // adjoint seed and the per-face gradient sums
         if ((s2 = op([=](cudaStream_t q) {
                  cudaError_t e = cudaMemcpyAsync(LM, LT, nb, cudaMemcpyDeviceToDevice, q);
-                 if (e == cudaSuccess) e = cudaMemsetAsync(GK, 0, nb, q);
+                 if (e == cudaSuccess) e = cudaMemsetAsync(FACE, 0, face_bytes, q);
                  return e;
              })))
             return s2;
@@ -491,23 +495,29 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
                 double *lout = (t == 0) ? GU : LM + (size_t)(li ^ 1) * n;
                 if (mode == HXC_MODE_PLAIN) {
                     if ((s2 = op([=](cudaStream_t q) {
-                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, GK, c, ny, nx, false, true, q);
+                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, false, true, q);
                          })))
                         return s2;
                     if ((s2 = op([=](cudaStream_t q) {
-                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, GK, c, ny, nx, true, false, q);
+                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, true, false, q);
                          })))
                         return s2;
                     sc.launch(2);
                 } else {
                     if ((s2 = op([=](cudaStream_t q) {
-                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, GK, c, ny, nx, true, true, q);
+                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, true, true, q);
                          })))
                         return s2;
                     sc.launch();
                 }
                 li ^= 1;
             }
+        }
+        if (steps > 0) {
+            // dL/dkappa from the face sums
+            if ((s2 = op([=](cudaStream_t q) { return k::vc_face_combine(FACE, GK, c, ny, nx, q); })))
+                return s2;
+            sc.launch();
         }
         if (steps == 0) {
             if ((s2 = op([=](cudaStream_t q) {
@@ -525,7 +535,7 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
     FutRef last;
     if (mode == HXC_MODE_GRAPH) {
         std::string key = key_of("adjoint", {(double)ny, (double)nx, c, (double)steps, (double)every},
-                                 {U0, K, LT, GK, GU, UT, WE, CK, SEG, WK, LM});
+                                 {U0, K, LT, GK, GU, UT, WE, CK, SEG, WK, LM, FACE});
         Ref<Graph> g;
         auto capture = [&](int64_t *kernels) {
             hxc_run_stats cnt{};

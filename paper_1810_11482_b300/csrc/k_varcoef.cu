@@ -18,11 +18,20 @@
 // (products and differences issued as fused multiply-adds that round
 // identically, see Fk below).
 // with zero neighbours (and zero weights) outside the field.
-// Canonical kappa-gradient of one step, given u = u^n and l = lambda^{n+1}:
-//   d_f = u_b - u_a, l_f = l_a - l_b (u_b = l_b = 0 outside), doubled d_f on
-//   boundary faces; S = fma(dW, lW, fma(dE, lE, fma(dN, lN, dS * lS)));
-//   gk_a = fma(c/2, S, gk_a)
-// i.e. dL/dkappa_a = sum_f dk_f/dkappa_a * c (u_b - u_a)(l_a - l_b).
+// Canonical kappa-gradient, dL/dkappa_a = sum_n sum_f dk_f/dkappa_a *
+// c (u_b - u_a)(l_a - l_b) with u = u^n, l = lambda^{n+1} (u_b = l_b = 0
+// outside; dk_f/dkappa_a = 1/2 on an interior face, 1 on a boundary face).
+// The face product p_f = (u_b - u_a)(l_a - l_b) is the same seen from either
+// cell of the face, so it is formed once per face and step and summed over
+// the steps per face:
+//   GE[a] += p(a, east face), GS[a] += p(a, south face)   (every cell; the
+//     east/south face of the last column/row is a boundary face, ghost 0),
+//   GW0[i] += p((i,0), west face), GN0[j] += p((0,j), north face),
+// each as fma(fma(u_a, -1, u_b), fma(l_b, -1, l_a), G).  After the last step
+//   gk_a = (c/2) * ((W + E) + (N + S)),
+// E = GE[a] (x2 on the east boundary), W = GE[a-1] (x2 GW0[i] on the west
+// boundary), S = GS[a] (x2 on the south boundary), N = GS[a-nx] (x2 GN0[j]
+// on the north boundary).  Per cell and step: 6 FP64 operations.
 #include "kernels.cuh"
 #include "tune.hpp"
 
@@ -158,45 +167,77 @@ __global__ void k_vc_step_otf(const double *__restrict__ u, double *__restrict__
     }
 }
 
-// kappa-gradient contribution of one step at cell (i, j).
-__device__ __forceinline__ double vc_grad_sum(const double *__restrict__ u,
-                                              const double *__restrict__ lam, int64_t ny,
-                                              int64_t nx, int64_t i, int64_t j, Fk f) {
-    const int64_t a = i * nx + j;
-    const double ua = u[a], la = lam[a];
-    const double db = __fma_rn(-2.0, ua, f.nz);  // boundary face: 2 (0 - u_a)
-    const double dW = j > 0 ? __fma_rn(ua, f.mone, u[a - 1]) : db;
-    const double lW = j > 0 ? __fma_rn(lam[a - 1], f.mone, la) : la;
-    const double dE = j + 1 < nx ? __fma_rn(ua, f.mone, u[a + 1]) : db;
-    const double lE = j + 1 < nx ? __fma_rn(lam[a + 1], f.mone, la) : la;
-    const double dN = i > 0 ? __fma_rn(ua, f.mone, u[a - nx]) : db;
-    const double lN = i > 0 ? __fma_rn(lam[a - nx], f.mone, la) : la;
-    const double dS = i + 1 < ny ? __fma_rn(ua, f.mone, u[a + nx]) : db;
-    const double lS = i + 1 < ny ? __fma_rn(lam[a + nx], f.mone, la) : la;
-    return __fma_rn(dW, lW, __fma_rn(dE, lE, __fma_rn(dN, lN, __fma_rn(dS, lS, f.nz))));
+// Face product (u_b - u_a)(l_a - l_b) accumulated into g (see above).
+__device__ __forceinline__ double face_acc(double ua, double la, double ub, double lb, double g,
+                                           Fk f) {
+    return __fma_rn(__fma_rn(ua, f.mone, ub), __fma_rn(lb, f.mone, la), g);
 }
 
-// Adjoint step fused with the kappa-gradient accumulation (either part can
-// be switched off to launch them separately).
+// Face-sum arrays of the kappa-gradient: GE (n), GS (n), GW0 (ny), GN0 (nx).
+struct FaceSums {
+    double *GE, *GS, *GW0, *GN0;
+};
+
+__device__ __forceinline__ FaceSums face_sums(double *face, int64_t ny, int64_t nx) {
+    const int64_t n = ny * nx;
+    return FaceSums{face, face + n, face + 2 * n, face + 2 * n + ny};
+}
+
+// Per-face kappa-gradient accumulation of one step at cell (i, j).
+__device__ __forceinline__ void vc_face_step(const double *__restrict__ u,
+                                             const double *__restrict__ lam, FaceSums g,
+                                             int64_t ny, int64_t nx, int64_t i, int64_t j, Fk f) {
+    const int64_t a = i * nx + j;
+    const double ua = u[a], la = lam[a];
+    const bool e = j + 1 < nx, so = i + 1 < ny;
+    const double uE = e ? u[a + 1] : 0.0, lE = e ? lam[a + 1] : 0.0;
+    const double uS = so ? u[a + nx] : 0.0, lS = so ? lam[a + nx] : 0.0;
+    g.GE[a] = face_acc(ua, la, uE, lE, g.GE[a], f);
+    g.GS[a] = face_acc(ua, la, uS, lS, g.GS[a], f);
+    if (j == 0) g.GW0[i] = face_acc(ua, la, 0.0, 0.0, g.GW0[i], f);
+    if (i == 0) g.GN0[j] = face_acc(ua, la, 0.0, 0.0, g.GN0[j], f);
+}
+
+// Adjoint step fused with the per-face kappa-gradient accumulation (either
+// part can be switched off to launch them separately).
 __global__ void k_vc_adjoint(const double *__restrict__ lam, double *__restrict__ lam_out,
                              const double *__restrict__ u, const double *__restrict__ wE,
                              const double *__restrict__ wS, const double *__restrict__ m,
-                             double *__restrict__ gk, double ch, int64_t ny, int64_t nx,
-                             int do_lam, int do_grad, Fk f) {
+                             double *face, int64_t ny, int64_t nx, int do_lam, int do_grad,
+                             Fk f) {
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t segs = (nx + 31) / 32;
+    const FaceSums g = face_sums(face, ny, nx);
     for (int64_t w = blockIdx.x * wpb + (threadIdx.x >> 5); w < ny * segs;
          w += (int64_t)gridDim.x * wpb) {
         const int64_t i = w / segs, j = (w % segs) * 32 + lane;
         if (j >= nx) continue;
-        const int64_t a = i * nx + j;
-        if (do_lam) lam_out[a] = vc_step_at(lam, wE, wS, m, ny, nx, i, j, f);
-        if (do_grad) gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j, f), gk[a]);
+        if (do_lam) lam_out[i * nx + j] = vc_step_at(lam, wE, wS, m, ny, nx, i, j, f);
+        if (do_grad) vc_face_step(u, lam, g, ny, nx, i, j, f);
     }
 }
 
-// Adjoint step with on-the-fly coefficients (the hxc_launch kernel).
+// gk from the face sums after the last step (see above).
+__global__ void k_vc_face_combine(const double *face, double *__restrict__ gk, double ch,
+                                  int64_t ny, int64_t nx) {
+    const int64_t n = ny * nx;
+    const FaceSums g = face_sums(const_cast<double *>(face), ny, nx);
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a / nx, j = a % nx;
+        const double E = j + 1 < nx ? g.GE[a] : __dmul_rn(2.0, g.GE[a]);
+        const double W = j > 0 ? g.GE[a - 1] : __dmul_rn(2.0, g.GW0[i]);
+        const double S = i + 1 < ny ? g.GS[a] : __dmul_rn(2.0, g.GS[a]);
+        const double N = i > 0 ? g.GS[a - nx] : __dmul_rn(2.0, g.GN0[j]);
+        gk[a] = __dmul_rn(ch, __dadd_rn(__dadd_rn(W, E), __dadd_rn(N, S)));
+    }
+}
+
+// Adjoint step with on-the-fly coefficients (the hxc_launch kernel): one
+// step's face products, doubled on boundary faces, combined and accumulated
+// per step, gk_a = fma(c/2, (W + E) + (N + S), gk_a) -- from gk = 0 the same
+// bits as a one-step adjoint run.
 __global__ void k_vc_adjoint_otf(const double *__restrict__ lam, double *__restrict__ lam_out,
                                  const double *__restrict__ u, const double *__restrict__ kap,
                                  double *__restrict__ gk, double c, int64_t ny, int64_t nx,
@@ -209,10 +250,24 @@ __global__ void k_vc_adjoint_otf(const double *__restrict__ lam, double *__restr
         const VcCoef q = vc_coef_at(kap, c, ny, nx, i, j);
         const double wW = j > 0 ? vc_coef_at(kap, c, ny, nx, i, j - 1).wE : 0.0;
         const double wN = i > 0 ? vc_coef_at(kap, c, ny, nx, i - 1, j).wS : 0.0;
+        const double la = lam[a], ua = u[a];
         const double lW = j > 0 ? lam[a - 1] : 0.0, lE = j + 1 < nx ? lam[a + 1] : 0.0;
         const double lN = i > 0 ? lam[a - nx] : 0.0, lS = i + 1 < ny ? lam[a + nx] : 0.0;
-        lam_out[a] = vc_update(lam[a], lW, lE, lN, lS, wW, q.wE, wN, q.wS, q.m, f);
-        gk[a] = __fma_rn(ch, vc_grad_sum(u, lam, ny, nx, i, j, f), gk[a]);
+        const double uW = j > 0 ? u[a - 1] : 0.0, uE = j + 1 < nx ? u[a + 1] : 0.0;
+        const double uN = i > 0 ? u[a - nx] : 0.0, uS = i + 1 < ny ? u[a + nx] : 0.0;
+        lam_out[a] = vc_update(la, lW, lE, lN, lS, wW, q.wE, wN, q.wS, q.m, f);
+        // each face product as the face's own cells form it (the west and
+        // north faces from the neighbour's side: both factors change sign,
+        // the rounded product does not)
+        const double pE = face_acc(ua, la, uE, lE, 0.0, f);
+        const double pS = face_acc(ua, la, uS, lS, 0.0, f);
+        const double pW = j > 0 ? face_acc(uW, lW, ua, la, 0.0, f) : face_acc(ua, la, 0.0, 0.0, 0.0, f);
+        const double pN = i > 0 ? face_acc(uN, lN, ua, la, 0.0, f) : face_acc(ua, la, 0.0, 0.0, 0.0, f);
+        const double E = j + 1 < nx ? pE : __dmul_rn(2.0, pE);
+        const double W = j > 0 ? pW : __dmul_rn(2.0, pW);
+        const double S = i + 1 < ny ? pS : __dmul_rn(2.0, pS);
+        const double N = i > 0 ? pN : __dmul_rn(2.0, pN);
+        gk[a] = __fma_rn(ch, __dadd_rn(__dadd_rn(W, E), __dadd_rn(N, S)), gk[a]);
     }
 }
 
@@ -267,12 +322,19 @@ struct VcProblem {
 // Persistent batch kernel: every CTA takes whole problems from a work queue
 // (largest first) and runs all `steps` steps of a problem before taking the
 // next one, so the batch is a single launch with no device-wide barrier.
-// The CTA computes the problem's coefficients into wE/wS/m first; steps
-// ping-pong between u and tmp; an odd step count ends with a copy into u.
+// The CTA computes the problem's coefficients into wE/wS/m first.  A problem
+// of side <= smem_side keeps both of its fields in shared memory for all its
+// steps (2 side^2 doubles of dynamic shared memory; the coefficients stay in
+// global memory, where their few KB remain in L1/L2), so u is read and
+// written in global memory once per run; larger problems ping-pong between u
+// and tmp in global memory and an odd step count ends with a copy into u.
+// Both paths evaluate the same canonical update in the same order.
 __global__ void __launch_bounds__(1024) k_vc_batch(const VcProblem *__restrict__ probs, int nprob,
                                                   unsigned *queue, double *u, double *tmp,
                                                   const double *__restrict__ kap, double *wE,
-                                                  double *wS, double *m, int steps, Fk f) {
+                                                  double *wS, double *m, int steps, int smem_side,
+                                                  Fk f) {
+    extern __shared__ double vc_sm[];
     __shared__ int item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (;;) {
@@ -290,6 +352,24 @@ __global__ void __launch_bounds__(1024) k_vc_batch(const VcProblem *__restrict__
             pe[a] = q.wE;
             ps[a] = q.wS;
             pm[a] = q.m;
+        }
+        if (s <= smem_side) {
+            // shared-memory resident: both fields on chip for all steps
+            double *sa = vc_sm, *sb = vc_sm + n;
+            for (int64_t a = threadIdx.x; a < n; a += blockDim.x) sa[a] = pu[a];
+            __syncthreads();
+            for (int st = 0; st < steps; st++) {
+                const double *src = (st & 1) ? sb : sa;
+                double *dst = (st & 1) ? sa : sb;
+                for (int64_t i = warp; i < s; i += nw)
+                    for (int64_t j = lane; j < s; j += 32)
+                        dst[i * s + j] = vc_step_at(src, pe, ps, pm, s, s, i, j, f);
+                __syncthreads();
+            }
+            const double *fin = (steps & 1) ? sb : sa;
+            for (int64_t a = threadIdx.x; a < n; a += blockDim.x) pu[a] = fin[a];
+            __syncthreads();
+            continue;
         }
         __syncthreads();
         for (int st = 0; st < steps; st++) {
@@ -358,6 +438,8 @@ __global__ void k_vc_batch_step(const VcProblem *__restrict__ probs, const int64
 
 // ---------------------------------------------------------------- launchers
 static const Fk kF{-0.0, -1.0};
+// largest shared-memory-resident problem side (2 fields fill 226.6 KB)
+constexpr int kBatchSmemMaxSide = 119;
 
 static unsigned grid_for(int64_t work, unsigned per_block, const hxc_launch_cfg *cfg) {
     if (cfg) return cfg->grid[0] * cfg->grid[1] * cfg->grid[2];
@@ -396,11 +478,19 @@ cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c
 }
 
 cudaError_t vc_adjoint(const double *lam, double *lam_out, const double *u, const double *wE,
-                       const double *wS, const double *m, double *gk, double c, int64_t ny,
-                       int64_t nx, bool do_lam, bool do_grad, cudaStream_t s) {
+                       const double *wS, const double *m, double *face, int64_t ny, int64_t nx,
+                       bool do_lam, bool do_grad, cudaStream_t s) {
     const int64_t work = ny * ((nx + 31) / 32);
-    k_vc_adjoint<<<grid_for(work, 8, nullptr), 256, 0, s>>>(lam, lam_out, u, wE, wS, m, gk,
-                                                          0.5 * c, ny, nx, do_lam, do_grad, kF);
+    k_vc_adjoint<<<grid_for(work, 8, nullptr), 256, 0, s>>>(lam, lam_out, u, wE, wS, m, face, ny,
+                                                          nx, do_lam, do_grad, kF);
+    return cudaGetLastError();
+}
+
+size_t vc_face_doubles(int64_t ny, int64_t nx) { return (size_t)(2 * ny * nx + ny + nx); }
+
+cudaError_t vc_face_combine(const double *face, double *gk, double c, int64_t ny, int64_t nx,
+                            cudaStream_t s) {
+    k_vc_face_combine<<<grid_for(ny * nx, 256, nullptr), 256, 0, s>>>(face, gk, 0.5 * c, ny, nx);
     return cudaGetLastError();
 }
 
@@ -429,8 +519,17 @@ cudaError_t vc_batch_persistent(const void *probs, int nprob, unsigned *queue, d
     if (e != cudaSuccess) return e;
     const int g = sm_count() * (ctas_per_sm > 0 ? ctas_per_sm : (int)tune::get("batch.ctas_per_sm"));
     const int b = (int)tune::get("batch.block") / 32 * 32;  // whole warps
-    k_vc_batch<<<g, b, 0, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
-                                  wE, wS, m, steps, kF);
+    const int side = (int)tune::get("batch.smem_side");
+    const size_t smem = (size_t)2 * side * side * sizeof(double);
+    static std::atomic<uint64_t> attr{0};
+    if (smem > 48 * 1024) {
+        // the largest accepted side needs all of a CTA's shared memory
+        e = smem_optin(k_vc_batch, 2 * kBatchSmemMaxSide * kBatchSmemMaxSide * (int)sizeof(double),
+                       attr);
+        if (e != cudaSuccess) return e;
+    }
+    k_vc_batch<<<g, b, smem, s>>>(static_cast<const VcProblem *>(probs), nprob, queue, u, tmp, kap,
+                                  wE, wS, m, steps, side, kF);
     return cudaGetLastError();
 }
 

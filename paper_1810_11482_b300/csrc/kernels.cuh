@@ -99,9 +99,16 @@ cudaError_t vc_step(const double *u, double *un, const double *wE, const double 
                     const double *m, int64_t ny, int64_t nx, cudaStream_t s);
 cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c, int64_t ny,
                         int64_t nx, const hxc_launch_cfg *cfg, cudaStream_t s);
+// Adjoint step (do_lam) and per-face kappa-gradient accumulation (do_grad)
+// into face = [GE (n) | GS (n) | GW0 (ny) | GN0 (nx)] (vc_face_doubles(ny,
+// nx) doubles, zero before the first step); vc_face_combine turns the face
+// sums into gk after the last step.
 cudaError_t vc_adjoint(const double *lam, double *lam_out, const double *u, const double *wE,
-                       const double *wS, const double *m, double *gk, double c, int64_t ny,
-                       int64_t nx, bool do_lam, bool do_grad, cudaStream_t s);
+                       const double *wS, const double *m, double *face, int64_t ny, int64_t nx,
+                       bool do_lam, bool do_grad, cudaStream_t s);
+size_t vc_face_doubles(int64_t ny, int64_t nx);
+cudaError_t vc_face_combine(const double *face, double *gk, double c, int64_t ny, int64_t nx,
+                            cudaStream_t s);
 cudaError_t vc_adjoint_otf(const double *lam, double *lam_out, const double *u, const double *kap,
                            double *gk, double c, int64_t ny, int64_t nx, const hxc_launch_cfg *cfg,
                            cudaStream_t s);
