@@ -32,9 +32,12 @@ Knob g_knobs[] = {
     {"heat3d.variant", 4, 0, 4},      // 0 copied, 1 rotated, 2 rotated + f32x2, 3 two-plane, 4 + ring
     {"heat3d.variant1", 5, 0, 5},     // the same choice for one-step launches, 5 = streaming one-step kernel
     {"heat1d.tb_ctas", 0, 0, 1 << 16},  // CTAs per partition of the 1D blocked kernel (0: SMs/parts)
+    {"heat1d.steps_per_launch", 0, 0, 1024},  // fused 1D steps per launch when the caller passes 0 (0: all)
+    {"heat3d.steps_per_launch", 4, 1, 4},     // fused 3D steps per launch when the caller passes 0
     {"mandel.pair", 1, 0, 1},         // Mandelbrot: 1 = two pixels per thread on paired FP32
     {"batch.ctas_per_sm", 4, 1, 16},  // CTAs per SM of the persistent batch kernel
     {"batch.block", 256, 256, 1024},  // threads per CTA of the persistent batch kernel
+    {"batch.smem_side", 0, 0, 119},   // largest side kept in shared memory for a whole run (0: none)
 };
 std::mutex g_m;
 

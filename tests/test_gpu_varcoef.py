@@ -92,6 +92,28 @@ def test_batch_small_vs_oracle_all_modes(dev):
         assert np.array_equal(outs["plain"], outs["fused"])
 
 
+def test_batch_smem_resident_problems_bit_identical(dev):
+    """Problems up to the side set by batch.smem_side run with both fields
+    in shared memory for the whole run: the persistent launch gives the
+    same bits for every threshold (none, some, all problems resident), for
+    even and odd step counts, as the per-step schedule."""
+    sides = np.array([1, 2, 31, 32, 33, 40, 59, 64, 70, 97, 119, 120, 150, 7, 64, 1], dtype=np.int64)
+    sides, offs, kap, u0, cs = synth.batch_input(seed=411, sides=sides)
+    old = hxc.tune_get("batch.smem_side")
+    try:
+        for steps in (1, 6, 9):
+            want = oracle.varcoef2d_batch(u0, kap, sides, offs, cs, steps)
+            ref, _ = run_batch(dev, sides, kap, u0, cs, steps, "graph")
+            assert rel(ref, want) <= TOL
+            for side in (0, 32, 59, 119):
+                hxc.tune_set("batch.smem_side", side)
+                got, st = run_batch(dev, sides, kap, u0, cs, steps, "fused")
+                assert st.kernel_launches == 1
+                assert np.array_equal(got, ref), (steps, side)
+    finally:
+        hxc.tune_set("batch.smem_side", old)
+
+
 def test_batch_full_config(dev):
     """4096 problems, sides log-uniform in [32, 1024], kappa U[0.5, 1.5),
     c at 0.9 of the stability limit, 50 steps: fused (one persistent launch)
@@ -253,7 +275,9 @@ def test_adjoint_full_size_vs_oracle(dev):
     uT, lam, loss_b = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(8)
     hxc.varcoef_forward_run(dev, bu0, bk, n, n, c, steps, uT)[0].get()
     hxc.sqerr_seed(dev, uT, bt, lam, loss_b, n * n).get()
-    assert abs(down(loss_b, 1)[0] - oloss) <= 1e-12 * oloss
+    # the oracle adds the 2048^2 squares one after the other: relative error
+    # bound n 2^-53 = 4.7e-10 (the GPU's fixed-order tree is far tighter)
+    assert abs(down(loss_b, 1)[0] - oloss) <= 4.7e-10 * oloss
     for mode in ("fused", "plain"):
         gk, gu, _, _ = adjoint(dev, u0, kap, down(lam, u0.shape), c, steps, every, mode)
         assert rel(gk, ogk) <= TOLG, mode
