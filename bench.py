@@ -561,9 +561,10 @@ def secondary(dev, timer, peaks):
         res[mode] = {"ms": ms, "gradient_updates_per_s": n2 * n2 * st4 / (ms / 1e3)}
     speedups(res)
     res["gradient_over_forward_time"] = res["fused"]["ms"] / res["forward"]["ms"]
-    res["roofline"] = fp64_roof(29 * n2 * n2 * st4, res["fused"]["ms"], peaks,
-                                "29 FP64 operations per cell-step: forward with checkpoints 5, "
-                                "segment recompute 5, adjoint step 5, kappa-gradient 14; fused")
+    res["roofline"] = fp64_roof(21 * n2 * n2 * st4, res["fused"]["ms"], peaks,
+                                "21 FP64 operations per cell-step: forward with checkpoints 5, "
+                                "segment recompute 5, adjoint step 5, kappa-gradient face "
+                                "products 6; fused")
     res["forward"]["roofline"] = fp64_roof(5 * n2 * n2 * st4, res["forward"]["ms"], peaks,
                                            "5 FP64 operations per update")
     out["adjoint_2048^2_500steps_f64"] = res

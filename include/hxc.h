@@ -430,8 +430,9 @@ typedef struct {
  * result; tmp is scratch of the same size.  Each partition reads a halo from
  * its neighbours: in PLAIN and GRAPH mode step s of partition p runs after
  * step s-1 of p-1, p and p+1; FUSED mode advances `steps_per_launch` steps
- * per launch (0: all steps in one launch).  Results are bit-identical for
- * every partition count and mode. */
+ * per launch (0: the tuned count, knob heat1d.steps_per_launch, whose
+ * default 0 puts all steps in one launch).  Results are bit-identical for
+ * every partition count, mode and steps per launch. */
 hxc_status hxc_heat1d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, int64_t n, int parts,
                           double r, int steps, hxc_mode mode, int steps_per_launch,
                           const hxc_future *deps, int ndeps, hxc_future *out,
@@ -494,7 +495,8 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dev, const double *host_u0, doub
 /* 3D periodic FTCS in FP32 on an nz x ny x nx field (x fastest): u holds
  * the initial field and receives the result, tmp is scratch of the same
  * size.  PLAIN launches one step at a time, FUSED advances
- * `steps_per_launch` (1..4, 0 = 4) steps per launch with temporal blocking,
+ * `steps_per_launch` (1..4; 0: the tuned count, knob heat3d.steps_per_launch,
+ * default 4) steps per launch with temporal blocking,
  * GRAPH captures the fused launches once and replays them.  All modes give
  * bit-identical results. */
 /* The host half of the norms (a then-continuation of every snapshot in
@@ -608,12 +610,20 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *                  fields without a launch cfg, else form 3), the default.
  *   "heat1d.tb_ctas"  CTAs per partition of the temporally blocked 1D
  *                  kernel, 0 = SMs / partitions.
+ *   "heat1d.steps_per_launch"  steps per fused 1D launch when the caller
+ *                  passes 0, 0..1024 (default 0 = all steps in one launch).
+ *   "heat3d.steps_per_launch"  steps per fused 3D launch when the caller
+ *                  passes 0, 1..4 (default 4).
  *   "mandel.pair"  Mandelbrot kernel form: 1 = two horizontally adjacent
  *                  pixels per thread on paired FP32 instructions (default),
  *                  0 = one pixel per thread.
  *   "batch.ctas_per_sm"  CTAs per SM of the persistent batch kernel (4).
  *   "batch.block"  threads per CTA of the persistent batch kernel: 256 (default),
  *                  512 or 1024; blocks x CTAs per SM must fit the SM.
+ *   "batch.smem_side"  the persistent batch kernel keeps both fields of a
+ *                  problem of side <= this value in shared memory for the
+ *                  whole run (2 side^2 doubles per CTA), 0..119 (default 0:
+ *                  none).
  * Returns HXC_E_INVALID for an unknown key. */
 hxc_status hxc_tune_set(const char *key, int64_t value);
 hxc_status hxc_tune_get(const char *key, int64_t *value);

@@ -5,7 +5,10 @@ GPU and writes them to a JSON tuning cache.
 
 Knobs (see hxc_tune_set in include/hxc.h) change speed only -- every value
 gives bit-identical results -- so the search simply times each candidate on
-representative synthetic work with CUDA events and keeps the fastest.  The
+representative synthetic work with CUDA events and keeps the fastest: launch
+shapes of the 2D, 3D, 1D and batch kernels, the 3D kernel form, the steps
+per fused launch of the 1D and 3D runs, and the side below which the batch
+kernel keeps a problem in shared memory.  The
 cache maps "sm_<major><minor>" to {knob: value}; the library loads it when it
 first opens a device (HXC_TUNE_CACHE, else tune_cache.json beside
 libhxc.so).
@@ -108,6 +111,10 @@ def tune(quick=False, log=print):
     # one-step launches (PLAIN mode) choose their form separately
     run31 = lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 8, "plain", 1, d)[0]
     result.update(_search(timer, {"heat3d.variant1": [0, 1, 2, 3, 4, 5]}, run31, log))
+    # steps per fused launch when the caller passes 0 (12 steps: whole
+    # launches for 2, 3 and 4)
+    run3t = lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 12, "fused", 0, d)[0]
+    result.update(_search(timer, {"heat3d.steps_per_launch": [2, 3, 4]}, run3t, log))
     del a, b
     # 1D: CTAs per partition of the temporally blocked kernel
     n1 = 1 << 20
@@ -115,9 +122,11 @@ def tune(quick=False, log=print):
     p, q = dev.buffer(n1 * 8), dev.buffer(n1 * 8)
     p.write(v0).get()
     log("heat1d")
-    result.update(_search(timer, {"heat1d.tb_ctas": [0, 8, 12, 16, 18, 24, 32]},
-                          lambda d: hxc.heat1d_run(dev, p, q, n1, 8, 0.25, 100, "fused", 0, d)[0],
-                          log))
+    run1 = lambda d: hxc.heat1d_run(dev, p, q, n1, 8, 0.25, 100, "fused", 0, d)[0]
+    result.update(_search(timer, {"heat1d.tb_ctas": [0, 8, 12, 16, 18, 24, 32]}, run1, log))
+    # steps per fused launch (the caller's 0): all steps, or launches of
+    # fewer steps (smaller halos, more launches)
+    result.update(_search(timer, {"heat1d.steps_per_launch": [0, 10, 25, 50]}, run1, log))
     # batch: CTAs per SM of the persistent kernel, on the full batch (its
     # largest problems set the critical path of the
     # persistent kernel, so a subset would tune for a different balance)
@@ -126,9 +135,14 @@ def tune(quick=False, log=print):
     bu.write(ub).get()
     bk.write(kap).get()
     log("batch")
+    runb = lambda d: hxc.varcoef_batch_run(dev, bu, bk, sides, cs, 50, "fused", d)[0]
     result.update(_search(timer, {"batch.block": [256, 512], "batch.ctas_per_sm": [1, 2, 3, 4]},
-                          lambda d: hxc.varcoef_batch_run(dev, bu, bk, sides, cs, 50, "fused", d)[0],
-                          log))
+                          runb, log))
+    # shared-memory residency threshold of small problems (the CTAs per SM
+    # chosen above must still fit: 2 side^2 doubles per CTA)
+    fit = [v for v in (0, 32, 40, 48, 59)
+           if 2 * v * v * 8 * result["batch.ctas_per_sm"] <= 200 * 1024]
+    result.update(_search(timer, {"batch.smem_side": fit}, runb, log))
     return dev, result
 
 

@@ -155,7 +155,12 @@ hxc_status hxc_heat1d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
     Heat1dPlan pl{d.get(), {(double *)u->ptr, (double *)t->ptr}, n, split(n, parts, false), r};
     int T = 1;
     if (mode == HXC_MODE_FUSED) {
-        T = steps_per_launch == 0 ? std::min(steps, k::kHeat1dMaxSteps) : steps_per_launch;
+        if (steps_per_launch == 0) {
+            const int tuned = (int)tune::get("heat1d.steps_per_launch");
+            T = std::min(steps, tuned > 0 ? tuned : k::kHeat1dMaxSteps);
+        } else {
+            T = steps_per_launch;
+        }
         if (T < 1) T = 1;
     }
     std::vector<FutRef> finals;
@@ -283,32 +288,28 @@ struct HostNormTask {
     double *out;
 };
 
-// sqrt(sum v^2) of a snapshot tile on the host, accumulated in long double
-// (x87 extended precision, unit roundoff u = 2^-64): blocks of 1024 squares
-// are summed with 8 independent accumulators, the block sums pairwise.  The
-// squares of doubles and these sums of non-negative terms carry a relative
-// error below (1024/8 + 3 + log2(blocks) + 1) u ~ 8e-18 for a 1024^2 tile, so
-// the result is the exact norm correctly rounded to double within about
-// one part in 1e16 (the tolerance asked of the host norms against a
-// long-double reference sum is 1e-14).
+// sqrt(sum v^2) of a snapshot tile on the host.  The squares are rounded
+// to double (a vectorisable loop; relative error <= 2^-53 each) and summed in
+// long double (x87 extended precision, u = 2^-64): blocks of 1024 squares
+// with 8 independent accumulators, the block sums pairwise.  For these
+// non-negative terms the sum's relative error stays below
+// 2^-53 + (1024/8 + 3 + log2(blocks)) u ~ 1.2e-16, so the norm is within
+// about 2e-16 of the exact one after its final rounding (the tolerance asked
+// of the host norms against a long-double reference sum is 1e-14).
 hxc_status host_norm_fn(void *user) {
     HostNormTask *t = static_cast<HostNormTask *>(user);
     const double *x = t->data;
     const int64_t n = t->count, B = 1024;
     std::vector<long double> blocks((n + B - 1) / B);
+    double sq[B];
     for (int64_t b0 = 0, k = 0; b0 < n; b0 += B, k++) {
-        const int64_t e = std::min(n, b0 + B);
+        const int64_t m = std::min(B, n - b0);
+        for (int64_t i = 0; i < m; i++) sq[i] = x[b0 + i] * x[b0 + i];
         long double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int64_t i = b0;
-        for (; i + 8 <= e; i += 8)
-            for (int q = 0; q < 8; q++) {
-                const long double v = x[i + q];
-                a[q] += v * v;
-            }
-        for (; i < e; i++) {
-            const long double v = x[i];
-            a[0] += v * v;
-        }
+        int64_t i = 0;
+        for (; i + 8 <= m; i += 8)
+            for (int q = 0; q < 8; q++) a[q] += sq[i + q];
+        for (; i < m; i++) a[0] += sq[i];
         blocks[k] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     }
     for (size_t w = 1; w < blocks.size(); w *= 2)
@@ -1195,7 +1196,10 @@ hxc_status hxc_heat3d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
     }
     Stats stats{stats_out};
     if ((st = d->make_current())) return st;
-    const int T = mode == HXC_MODE_PLAIN ? 1 : (steps_per_launch == 0 ? 4 : steps_per_launch);
+    const int T = mode == HXC_MODE_PLAIN
+                      ? 1
+                      : (steps_per_launch == 0 ? (int)tune::get("heat3d.steps_per_launch")
+                                               : steps_per_launch);
     float *buf[2] = {(float *)u->ptr, (float *)t->ptr};
     const int inz = (int)nz, iny = (int)ny, inx = (int)nx;
     FutRef prev;
