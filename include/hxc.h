@@ -601,8 +601,13 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
  *                  2 x 4 cells per thread, 64 x 64 regions, the z range split
  *                  evenly over one CTA per SM, 4 = form 3 with the input
  *                  planes copied into a shared-memory ring two planes ahead
- *                  (default).  Forms 3 and 4 launched with an hxc_launch_cfg
- *                  take 512 threads per CTA and any grid.
+ *                  (default), 6 = form 4 with packed narrow tiles (the
+ *                  columns and rows left over by the 64 - 2T wide output
+ *                  tiles go to 16-wide regions run four or sixteen to a CTA
+ *                  in lane segments and warp groups).  Forms 3, 4 and 6
+ *                  launched with an hxc_launch_cfg take 512 threads per CTA
+ *                  and any grid (form 6 at least 2 CTAs when it has both
+ *                  kinds of tiles).
  *   "heat3d.variant1"  the form used for one-step launches (PLAIN mode and
  *                  single-step remainders), the values above plus 5 = a
  *                  streaming kernel (4 adjacent x cells per thread, 16-byte

@@ -675,7 +675,7 @@ __device__ __forceinline__ void v4_fetch(f2 *__restrict__ ring, int slot, const 
     cp_commit();
 }
 
-template <int T, int Q>
+template <int T, int Q, int SW>
 __device__ __forceinline__ void v4_iter(f2 (&X)[T][4], f2 (&Y)[T][4], f2 (&Pp)[T][4],
                                         f2 *__restrict__ ring, int slot, int fslot,
                                         f2 *__restrict__ Sb, const float *__restrict__ src,
@@ -724,8 +724,9 @@ __device__ __forceinline__ void v4_iter(f2 (&X)[T][4], f2 (&Y)[T][4], f2 (&Pp)[T
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const f2 v = N[t][k];
-            const float lft = __shfl_up_sync(0xffffffffu, hi_of(v), 1);
-            const float rgt = __shfl_down_sync(0xffffffffu, lo_of(v), 1);
+            // lanes exchange within segments of SW lanes (one region each)
+            const float lft = __shfl_up_sync(0xffffffffu, hi_of(v), 1, SW);
+            const float rgt = __shfl_down_sync(0xffffffffu, lo_of(v), 1, SW);
             // left cell: (left lane's high) + own high; right cell: own low + (right lane's low)
             const f2 xs = pk(__fadd_rn(lft, hi_of(v)), __fadd_rn(lo_of(v), rgt));
             const f2 ys = add2(k == 0 ? up : N[t][k - 1], k == 3 ? dn : N[t][k + 1]);
@@ -800,14 +801,14 @@ __global__ void __launch_bounds__(V3_NW * 32, 1)
         int slot = 0;
         for (int j = 0; j < iters; j += 2) {
             int fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
-            v4_iter<T, 0>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
+            v4_iter<T, 0, 32>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
                           zf, nz, plane, j >= 2 * T, za - 2 * T + j, omask, lane, warp, ru, rd, wu,
                           wd, r2, m6);
             buf ^= 1;
             slot = slot + 1 < V4_RS ? slot + 1 : 0;
             if (j + 1 >= iters) break;
             fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
-            v4_iter<T, 1>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
+            v4_iter<T, 1, 32>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
                           zf, nz, plane, j + 1 >= 2 * T, za - 2 * T + j + 1, omask, lane, warp, ru,
                           rd, wu, wd, r2, m6);
             buf ^= 1;
@@ -828,6 +829,231 @@ cudaError_t v4_launch(unsigned g, const float *src, float *dst, int nz, int ny, 
     if (e != cudaSuccess) return e;
     k_heat3d_v4<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r);
     return cudaGetLastError();
+}
+
+// Form 6: form 4 with packed narrow tiles.  Along each axis, full regions
+// are 64 cells wide (a warp's 32 lanes x 2 columns, or 16 warps x 4 rows)
+// and store their 64 - 2T central cells; the axis holds floor(n / (64 - 2T))
+// of them and the remainder goes to narrow regions 16 cells wide (8 lanes,
+// or 4 warps) that store 16 - 2T.  A CTA runs narrow regions four (narrow in
+// both axes: sixteen) at a time side by side in its lane segments and warp
+// groups, so no CTA computes a whole region for a few remaining columns:
+// 512 = 9 x 56 + 8 at T = 4 gives 88 region-sized units per plane instead
+// of the 100 of form 4.  Units: full x full (one region); narrow-x x full-y
+// (one narrow x tile, four y tiles in the four lane segments); full-x x
+// narrow-y (four x tiles in the four warp groups, one narrow y tile);
+// narrow x narrow (four x tiles by segment, four y tiles by group).
+//
+// The tiling of a launch, computed on the host and passed by value (kernel
+// parameters stay in the constant bank, so they cost no registers in the
+// register-bound level chain).  The units whose regions are 64 columns wide
+// take the CTAs [0, ctas_wide) and exchange x neighbours across all 32
+// lanes; the narrow-x units take the remaining CTAs, their lanes split into
+// segments of 8.  Each group splits its (unit, plane) pairs evenly over its
+// CTAs.
+struct Tiling3 {
+    int fx, fy, nxn, nyn;       // full and narrow tiles per axis
+    int fx4, fy4, nxn4, nyn4;   // the same in blocks of four (rounded up)
+    int ff, fn, nf, nn;         // units of each kind per plane
+    int ctas_wide;
+};
+
+inline Tiling3 tiling3(int ny, int nx, int T) {
+    const int fw = 64 - 2 * T, nw = 16 - 2 * T;
+    Tiling3 t;
+    t.fx = nx / fw;
+    t.fy = ny / fw;
+    t.nxn = (nx - t.fx * fw + nw - 1) / nw;
+    t.nyn = (ny - t.fy * fw + nw - 1) / nw;
+    t.fx4 = (t.fx + 3) / 4;
+    t.fy4 = (t.fy + 3) / 4;
+    t.nxn4 = (t.nxn + 3) / 4;
+    t.nyn4 = (t.nyn + 3) / 4;
+    t.ff = t.fx * t.fy;
+    t.fn = t.fx4 * t.nyn;
+    t.nf = t.nxn * t.fy4;
+    t.nn = t.nxn4 * t.nyn4;
+    t.ctas_wide = 0;
+    return t;
+}
+
+// Region of unit u for this thread: output origin (ox, oy), stored extent
+// wx x hy, gw warps per region, and whether the thread's slot holds a region
+// at all, packed as (ox, oy, wx | hy << 8, gw | valid << 8).  An empty slot
+// gets an origin inside the field and stores nothing.
+template <int T, int SW>
+__device__ __forceinline__ int4 v6_decode(int u, int ny, int nx, const Tiling3 &tl, int lane,
+                                          int warp) {
+    constexpr int FW = 64 - 2 * T, NWD = 16 - 2 * T;
+    int i, j, ox, oy, gw;
+    bool valid;
+    if (SW == 32) {
+        if (u < tl.ff) {
+            i = u % tl.fx;
+            j = u / tl.fx;
+            valid = true;
+            oy = j * FW;
+            gw = V3_NW;
+        } else {
+            u -= tl.ff;
+            i = 4 * (u % tl.fx4) + warp / 4;
+            j = u / tl.fx4;
+            valid = i < tl.fx;
+            oy = tl.fy * FW + j * NWD;
+            gw = 4;
+        }
+        ox = i * FW;
+    } else {
+        if (u < tl.nf) {
+            i = u % tl.nxn;
+            j = 4 * (u / tl.nxn) + lane / 8;
+            valid = j < tl.fy;
+            oy = j * FW;
+            gw = V3_NW;
+        } else {
+            u -= tl.nf;
+            i = 4 * (u % tl.nxn4) + lane / 8;
+            j = 4 * (u / tl.nxn4) + warp / 4;
+            valid = i < tl.nxn && j < tl.nyn;
+            oy = tl.fy * FW + j * NWD;
+            gw = 4;
+        }
+        ox = tl.fx * FW + i * NWD;
+    }
+    const int wx = valid ? min(SW == 32 ? FW : NWD, nx - ox) : 0;
+    const int hy = valid ? min(gw == V3_NW ? FW : NWD, ny - oy) : 0;
+    if (!valid) ox = oy = T;
+    return make_int4(ox, oy, wx | (hy << 8), gw | ((valid ? 1 : 0) << 8));
+}
+
+// The (unit, plane) pairs [w0, w1) of one group: SW = 32 for the wide
+// units, 8 for the narrow ones.
+template <int T, int SW>
+__device__ __forceinline__ void v6_units_run(const float *__restrict__ src, float *__restrict__ dst,
+                                             int nz, int ny, int nx, float r, const Tiling3 &tl,
+                                             int64_t w0, int64_t w1) {
+    constexpr int FW = 64 - 2 * T, NWD = 16 - 2 * T;
+    extern __shared__ __align__(16) f2 v4_smem[];
+    f2 *ring = v4_smem;
+    f2 *sbase = v4_smem + (size_t)V4_RS * V3_H * 32;
+    constexpr int SB = (T > 1 ? T - 1 : 1) * V3_NW * 2 * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t plane = (size_t)ny * nx;
+    const f2 r2 = pk(r, r), m6 = pk(-6.0f, -6.0f);
+    int buf = 0;
+
+    for (int64_t w = w0; w < w1;) {
+        int64_t u = w / nz;
+        const int za = (int)(w - u * nz);
+        const int zb = (int)min((int64_t)nz, za + (w1 - w));
+        w += zb - za;
+        // this thread's region of the unit (decoded out of line: inlined,
+        // the decode's temporaries push the level chain past the register
+        // budget)
+        const int4 geo = v6_decode<T, SW>((int)u, ny, nx, tl, lane, warp);
+        const int ox = geo.x, oy = geo.y, wx = geo.z & 0xff, hy = geo.z >> 8, gw = geo.w & 0xff;
+        const bool valid = (geo.w >> 8) != 0;
+        const int x0 = ox - T, y0 = oy - T;
+        const int ll = lane % SW, lw = warp % gw;
+        const int wu = lw > 0 ? warp - 1 : warp, wd = lw + 1 < gw ? warp + 1 : warp;
+        const int ru = lw > 0 ? 4 * warp - 1 : 4 * warp, rd = lw + 1 < gw ? 4 * warp + 4 : 4 * warp + 3;
+        const int c0 = 2 * ll;
+        const unsigned gx0 = wrapi(x0 + c0, nx), gx1 = wrapi(x0 + c0 + 1, nx);
+        const bool pair = gx1 == gx0 + 1 && (gx0 & 1u) == 0 && (nx & 1) == 0;
+        const bool ox0 = valid && c0 >= T && c0 < T + wx;
+        const bool ox1 = valid && c0 + 1 >= T && c0 + 1 < T + wx;
+        unsigned row[4], omask = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int q = 4 * lw + k;
+            row[k] = (unsigned)wrapi(y0 + q, ny) * (unsigned)nx;
+            const bool oy_ = q >= T && q < T + hy;
+            omask |= (oy_ && ox0 ? 1u : 0u) << (2 * k);
+            omask |= (oy_ && ox1 ? 2u : 0u) << (2 * k);
+        }
+
+        f2 X[T][4], Y[T][4], Pp[T][4];
+#pragma unroll
+        for (int t = 0; t < T; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) X[t][k] = Y[t][k] = Pp[t][k] = 0ull;
+        // iteration j receives level-0 plane za - T + j (ring slot j % V4_RS)
+        // and emits level-T plane za - 2T + j (stored for j >= 2T)
+        const int iters = (zb - za) + 2 * T;
+        int zf = wrapi(za - T, nz);
+        v4_fetch(ring, 0, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+#pragma unroll
+        for (int q = 1; q < V4_D; q++) {
+            zf = zf + 1 < nz ? zf + 1 : 0;
+            v4_fetch(ring, q, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+        }
+        int slot = 0;
+        for (int j = 0; j < iters; j += 2) {
+            int fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
+            v4_iter<T, 0, SW>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1,
+                              pair, zf, nz, plane, j >= 2 * T, za - 2 * T + j, omask, lane, warp,
+                              ru, rd, wu, wd, r2, m6);
+            buf ^= 1;
+            slot = slot + 1 < V4_RS ? slot + 1 : 0;
+            if (j + 1 >= iters) break;
+            fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
+            v4_iter<T, 1, SW>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1,
+                              pair, zf, nz, plane, j + 1 >= 2 * T, za - 2 * T + j + 1, omask, lane,
+                              warp, ru, rd, wu, wd, r2, m6);
+            buf ^= 1;
+            slot = slot + 1 < V4_RS ? slot + 1 : 0;
+        }
+        // the copies fetched past the segment land before the ring is reused
+        cp_wait<0>();
+        __syncthreads();
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(V3_NW * 32, 1)
+    k_heat3d_v6(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
+                float r, const Tiling3 tl) {
+    const int64_t work_wide = (int64_t)(tl.ff + tl.fn) * nz;
+    const int64_t work_narrow = (int64_t)(tl.nf + tl.nn) * nz;
+    const int64_t b = blockIdx.x;
+    if (b < tl.ctas_wide) {
+        const int64_t g = tl.ctas_wide;
+        v6_units_run<T, 32>(src, dst, nz, ny, nx, r, tl, work_wide * b / g, work_wide * (b + 1) / g);
+    } else {
+        const int64_t g = gridDim.x - tl.ctas_wide, c = b - tl.ctas_wide;
+        v6_units_run<T, 8>(src, dst, nz, ny, nx, r, tl, work_narrow * c / g,
+                           work_narrow * (c + 1) / g);
+    }
+}
+
+template <int T>
+cudaError_t v6_launch(unsigned g, const float *src, float *dst, int nz, int ny, int nx, float r,
+                      cudaStream_t s) {
+    constexpr size_t smem = v4_smem_bytes<T>();
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin(k_heat3d_v6<T>, (int)smem, attr);
+    if (e != cudaSuccess) return e;
+    Tiling3 tl = tiling3(ny, nx, T);
+    // CTAs in proportion to the work of the two groups (each group with
+    // work gets at least one CTA)
+    const int64_t wide = tl.ff + tl.fn, narrow = tl.nf + tl.nn;
+    if (narrow == 0) {
+        tl.ctas_wide = (int)g;
+    } else if (wide == 0) {
+        tl.ctas_wide = 0;
+    } else {
+        if (g < 2) g = 2;
+        const int64_t cw = (int64_t)g * wide / (wide + narrow);
+        tl.ctas_wide = (int)std::max<int64_t>(1, std::min<int64_t>(g - 1, cw));
+    }
+    k_heat3d_v6<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r, tl);
+    return cudaGetLastError();
+}
+
+// Units of work per plane of form 6.
+int64_t v6_units(int ny, int nx, int T) {
+    const Tiling3 t = tiling3(ny, nx, T);
+    return (int64_t)t.ff + t.fn + t.nf + t.nn;
 }
 
 int heat3d_blocks(int nz, int ny, int nx, int T, int zchunk) {
@@ -965,8 +1191,17 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
         if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != V3_NW * 32)
             return cudaErrorInvalidValue;
         const int BX = 64 - 2 * steps, BY = V3_H - 2 * steps;
-        const int64_t work = (int64_t)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
+        int64_t work = (int64_t)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
+        if (variant == 6) work = v6_units(ny, nx, steps) * nz;
         const unsigned g3 = cfg ? g : (unsigned)std::min<int64_t>(sm_count(), work);
+        if (variant == 6) {
+            switch (steps) {
+                case 1: return v6_launch<1>(g3, src, dst, nz, ny, nx, r, s);
+                case 2: return v6_launch<2>(g3, src, dst, nz, ny, nx, r, s);
+                case 3: return v6_launch<3>(g3, src, dst, nz, ny, nx, r, s);
+                case 4: return v6_launch<4>(g3, src, dst, nz, ny, nx, r, s);
+            }
+        }
         if (variant == 4) {
             switch (steps) {
                 case 1: return v4_launch<1>(g3, src, dst, nz, ny, nx, r, s);

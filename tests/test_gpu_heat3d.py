@@ -80,7 +80,7 @@ def test_heat3d_translation_and_reflection_exact(dev):
                               dtype=np.float32)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1")}
     try:
-        for variant in (2, 3, 4):
+        for variant in (2, 3, 4, 6):
             hxc.tune_set("heat3d.variant", variant)
             hxc.tune_set("heat3d.variant1", variant)
             ref, _ = run3d(dev, u0, 8, "fused", 4)
@@ -100,7 +100,8 @@ def test_heat3d_translation_and_reflection_exact(dev):
 def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     """Every form of the 3D kernel (plane registers copied, rotated, rotated
     with paired FP32 instructions, two planes per level with the z range split
-    over the CTAs, the same with a cp.async plane ring) and every z split give the bits of one plain step per launch
+    over the CTAs, the same with a cp.async plane ring, and with packed narrow
+    tiles) and every z split give the bits of one plain step per launch
     of the default form; odd nx takes the scalar-load path, small nz the
     wrapped z index."""
     u0 = synth.heat3d_input(shape[2], seed=330 + shape[0], nz=shape[0], ny=shape[1])
@@ -108,7 +109,7 @@ def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     want = oracle.heat3d(u0.astype(np.float64), float(R), 9)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1", "heat3d.zchunks")}
     try:
-        for variant in (0, 1, 2, 3, 4):
+        for variant in (0, 1, 2, 3, 4, 6):
             hxc.tune_set("heat3d.variant", variant)
             hxc.tune_set("heat3d.variant1", variant)
             for nch in (0, 1, 3):
@@ -182,7 +183,7 @@ def test_heat3d_full_size_windows(dev):
     # every two-plane form gives these bits at full size too
     old = hxc.tune_get("heat3d.variant")
     try:
-        for variant in (3, 4):
+        for variant in (3, 4, 6):
             hxc.tune_set("heat3d.variant", variant)
             other, _ = run3d(dev, u0, 200, "fused", 4)
             assert np.array_equal(other, got), variant
@@ -204,7 +205,7 @@ def test_heat3d_product_mode_full_size(dev):
 
 @pytest.mark.parametrize("shape", [(33, 200, 130), (5, 64, 64), (70, 57, 250)])
 def test_heat3d_two_plane_form_any_grid(dev, shape):
-    """The two-plane forms (variants 3 and 4) split the (region, plane) pairs
+    """The two-plane forms (variants 3, 4 and 6) split the (region, plane) pairs
     evenly over whatever grid they are launched with: one CTA, a few CTAs whose shares
     span several regions, and more CTAs than pairs (empty shares) all give the
     bits of the copied-plane form (variant 0); 1..4 steps per launch."""
@@ -216,7 +217,8 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
         for steps in (1, 2, 3, 4):
             want = None
             for variant, grid in ((0, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000),
-                                  (4, None), (4, 1), (4, 7), (4, 100000)):
+                                  (4, None), (4, 1), (4, 7), (4, 100000), (6, None), (6, 1),
+                                  (6, 7), (6, 100000)):
                 hxc.tune_set("heat3d.variant", variant)
                 hxc.tune_set("heat3d.variant1", variant)
                 a.write(u0).get()
