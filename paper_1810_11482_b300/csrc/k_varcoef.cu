@@ -183,7 +183,8 @@ __device__ __forceinline__ FaceSums face_sums(double *face, int64_t ny, int64_t 
     return FaceSums{face, face + n, face + 2 * n, face + 2 * n + ny};
 }
 
-// Per-face kappa-gradient accumulation of one step at cell (i, j).
+// Per-face kappa-gradient accumulation of one step at cell (i, j): its east
+// and south faces.
 __device__ __forceinline__ void vc_face_step(const double *__restrict__ u,
                                              const double *__restrict__ lam, FaceSums g,
                                              int64_t ny, int64_t nx, int64_t i, int64_t j, Fk f) {
@@ -194,6 +195,17 @@ __device__ __forceinline__ void vc_face_step(const double *__restrict__ u,
     const double uS = so ? u[a + nx] : 0.0, lS = so ? lam[a + nx] : 0.0;
     g.GE[a] = face_acc(ua, la, uE, lE, g.GE[a], f);
     g.GS[a] = face_acc(ua, la, uS, lS, g.GS[a], f);
+}
+
+// The west boundary face of a cell of column 0 and the north boundary face
+// of a cell of row 0.  Kept out of line and entered only by the warps that
+// hold such cells: inlined, the compiler predicates it into every warp,
+// where its FP64 operations still take the (narrow) FP64 pipe's cycles.
+__device__ __noinline__ void vc_face_edges(const double *__restrict__ u,
+                                           const double *__restrict__ lam, FaceSums g,
+                                           int64_t nx, int64_t i, int64_t j, Fk f) {
+    const int64_t a = i * nx + j;
+    const double ua = u[a], la = lam[a];
     if (j == 0) g.GW0[i] = face_acc(ua, la, 0.0, 0.0, g.GW0[i], f);
     if (i == 0) g.GN0[j] = face_acc(ua, la, 0.0, 0.0, g.GN0[j], f);
 }
@@ -211,10 +223,13 @@ __global__ void k_vc_adjoint(const double *__restrict__ lam, double *__restrict_
     const FaceSums g = face_sums(face, ny, nx);
     for (int64_t w = blockIdx.x * wpb + (threadIdx.x >> 5); w < ny * segs;
          w += (int64_t)gridDim.x * wpb) {
-        const int64_t i = w / segs, j = (w % segs) * 32 + lane;
+        const int64_t i = w / segs, seg = w % segs, j = seg * 32 + lane;
         if (j >= nx) continue;
         if (do_lam) lam_out[i * nx + j] = vc_step_at(lam, wE, wS, m, ny, nx, i, j, f);
-        if (do_grad) vc_face_step(u, lam, g, ny, nx, i, j, f);
+        if (do_grad) {
+            vc_face_step(u, lam, g, ny, nx, i, j, f);
+            if (seg == 0 || i == 0) vc_face_edges(u, lam, g, nx, i, j, f);  // warp-uniform
+        }
     }
 }
 
@@ -329,12 +344,35 @@ struct VcProblem {
 // written in global memory once per run; larger problems ping-pong between u
 // and tmp in global memory and an odd step count ends with a copy into u.
 // Both paths evaluate the same canonical update in the same order.
+// All steps of one problem with both fields in shared memory (the CTA's
+// dynamic shared memory, 2 s^2 doubles).  Out of line, so that the code of
+// the global-memory path of the batch kernel stays as it is without it.
+__device__ __noinline__ void vc_resident_problem(double *pu, const double *pe, const double *ps,
+                                                 const double *pm, int64_t s, int steps, Fk f) {
+    extern __shared__ double vc_sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t n = s * s;
+    double *sa = vc_sm, *sb = vc_sm + n;
+    for (int64_t a = threadIdx.x; a < n; a += blockDim.x) sa[a] = pu[a];
+    __syncthreads();
+    for (int st = 0; st < steps; st++) {
+        const double *src = (st & 1) ? sb : sa;
+        double *dst = (st & 1) ? sa : sb;
+        for (int64_t i = warp; i < s; i += nw)
+            for (int64_t j = lane; j < s; j += 32)
+                dst[i * s + j] = vc_step_at(src, pe, ps, pm, s, s, i, j, f);
+        __syncthreads();
+    }
+    const double *fin = (steps & 1) ? sb : sa;
+    for (int64_t a = threadIdx.x; a < n; a += blockDim.x) pu[a] = fin[a];
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(1024) k_vc_batch(const VcProblem *__restrict__ probs, int nprob,
                                                   unsigned *queue, double *u, double *tmp,
                                                   const double *__restrict__ kap, double *wE,
                                                   double *wS, double *m, int steps, int smem_side,
                                                   Fk f) {
-    extern __shared__ double vc_sm[];
     __shared__ int item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (;;) {
@@ -354,21 +392,7 @@ __global__ void __launch_bounds__(1024) k_vc_batch(const VcProblem *__restrict__
             pm[a] = q.m;
         }
         if (s <= smem_side) {
-            // shared-memory resident: both fields on chip for all steps
-            double *sa = vc_sm, *sb = vc_sm + n;
-            for (int64_t a = threadIdx.x; a < n; a += blockDim.x) sa[a] = pu[a];
-            __syncthreads();
-            for (int st = 0; st < steps; st++) {
-                const double *src = (st & 1) ? sb : sa;
-                double *dst = (st & 1) ? sa : sb;
-                for (int64_t i = warp; i < s; i += nw)
-                    for (int64_t j = lane; j < s; j += 32)
-                        dst[i * s + j] = vc_step_at(src, pe, ps, pm, s, s, i, j, f);
-                __syncthreads();
-            }
-            const double *fin = (steps & 1) ? sb : sa;
-            for (int64_t a = threadIdx.x; a < n; a += blockDim.x) pu[a] = fin[a];
-            __syncthreads();
+            vc_resident_problem(pu, pe, ps, pm, s, steps, f);
             continue;
         }
         __syncthreads();
