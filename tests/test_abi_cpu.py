@@ -228,8 +228,11 @@ def test_shipped_tuning_cache_parses(L):
     assert "sm_103" in data and set(data["sm_103"]) <= {"heat2d.emul", "heat2d.rows",
                                                         "heat2d.occupancy", "heat3d.zchunks",
                                                         "heat3d.variant", "heat3d.variant1",
-                                                        "heat1d.tb_ctas", "mandel.pair",
-                                                        "batch.ctas_per_sm", "batch.block"}
+                                                        "heat3d.steps_per_launch",
+                                                        "heat1d.tb_ctas",
+                                                        "heat1d.steps_per_launch", "mandel.pair",
+                                                        "batch.ctas_per_sm", "batch.block",
+                                                        "batch.smem_side"}
     hxc.tune_load(path, 10, 3)
     for k, v in data["sm_103"].items():
         assert hxc.tune_get(k) == v
