@@ -439,6 +439,11 @@ def summarize(sec):
         out["adjoint_ms"] = {m: r(a[m]["ms"]) for m in ("forward", "plain", "graph", "fused")}
         out["gradient_over_forward"] = r(a["gradient_over_forward_time"])
         out["adjoint_fused_speedup_vs_plain"] = r(a["fused"]["speedup_vs_plain"])
+        t = a.get("from_tape")
+        if t:
+            out["adjoint_from_tape_ms"] = {m: r(t[m]["ms"]) for m in ("forward_tape", "plain",
+                                                                      "graph", "fused")}
+            out["gradient_from_tape_over_forward"] = r(t["gradient_over_forward_time"])
     return out
 
 
@@ -561,6 +566,26 @@ def secondary(dev, timer, peaks):
         res[mode] = {"ms": ms, "gradient_updates_per_s": n2 * n2 * st4 / (ms / 1e3)}
     speedups(res)
     res["gradient_over_forward_time"] = res["fused"]["ms"] / res["forward"]["ms"]
+    # the training-step form: the forward pass keeps its checkpoint tape and
+    # the gradient starts from it (no second forward pass)
+    tape = dev.buffer(hxc.varcoef_tape_states(st4) * u0.nbytes)
+    ms = timed_run(lambda d: hxc.varcoef_forward_tape(dev, b0, bkk, n2, n2, c, st4, uT, tape,
+                                                      deps=[d] if d else ())[0])
+    tres = {"forward_tape": {"ms": ms}}
+    for mode in ("plain", "graph", "fused"):
+        ms = timed_run(lambda d, m=mode: hxc.varcoef_adjoint_tape(dev, tape, bkk, lam, n2, n2, c, st4,
+                                                                   gk, gu, 0, m, deps=[d] if d else ())[0])
+        tres[mode] = {"ms": ms, "speedup_vs_plain": None}
+    for m in ("plain", "graph", "fused"):
+        tres[m]["speedup_vs_plain"] = tres["plain"]["ms"] / tres[m]["ms"]
+    tres["gradient_over_forward_time"] = tres["fused"]["ms"] / res["forward"]["ms"]
+    tres["training_step_ms"] = tres["forward_tape"]["ms"] + tres["fused"]["ms"]
+    tres["training_step_ms_without_tape"] = res["forward"]["ms"] + res["fused"]["ms"]
+    tres["roofline"] = fp64_roof(16 * n2 * n2 * st4, tres["fused"]["ms"], peaks,
+                                 "16 FP64 operations per cell-step: segment recompute 5, adjoint "
+                                 "step 5, kappa-gradient face products 6; fused")
+    res["from_tape"] = tres
+    del tape
     res["roofline"] = fp64_roof(21 * n2 * n2 * st4, res["fused"]["ms"], peaks,
                                 "21 FP64 operations per cell-step: forward with checkpoints 5, "
                                 "segment recompute 5, adjoint step 5, kappa-gradient face "

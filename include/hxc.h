@@ -580,6 +580,31 @@ hxc_status hxc_varcoef_forward_run(hxc_device dev, hxc_buffer u0, hxc_buffer kap
                                    const hxc_future *deps, int ndeps, hxc_future *out,
                                    hxc_run_stats *stats);
 
+/* Checkpoint tapes (the paper has no counterpart; the forward pass of a
+ * training step keeps what its backward pass needs, as reverse-mode
+ * differentiation does).  A tape for `steps` steps checkpointed every
+ * `every` steps (0: ceil(sqrt(steps))) holds *states = max(1,
+ * ceil(steps / every)) fields of ny x nx doubles, checkpoint k being the
+ * state after k * every steps (checkpoint 0 = u0). */
+hxc_status hxc_varcoef_tape_states(int steps, int every, int64_t *states);
+/* hxc_varcoef_forward_run that also writes the tape (at least *states * ny
+ * * nx * 8 bytes; it must not overlap u0, kappa or uT).  The states are
+ * computed by the same kernels in the same order as the forward pass of
+ * hxc_varcoef_adjoint_run, so the two give the same bits. */
+hxc_status hxc_varcoef_forward_tape(hxc_device dev, hxc_buffer u0, hxc_buffer kappa, int64_t ny,
+                                    int64_t nx, double c, int steps, int every, hxc_buffer uT,
+                                    hxc_buffer tape, const hxc_future *deps, int ndeps,
+                                    hxc_future *out, hxc_run_stats *stats);
+/* hxc_varcoef_adjoint_run from a tape written by hxc_varcoef_forward_tape
+ * with the same kappa, c, steps and every: no forward pass, only the
+ * segment recomputations and the adjoint steps.  Results bit-identical to
+ * hxc_varcoef_adjoint_run's; the tape is read only. */
+hxc_status hxc_varcoef_adjoint_tape(hxc_device dev, hxc_buffer tape, hxc_buffer kappa,
+                                    hxc_buffer lamT, int64_t ny, int64_t nx, double c, int steps,
+                                    int every, hxc_mode mode, hxc_buffer gk, hxc_buffer gu0,
+                                    const hxc_future *deps, int ndeps, hxc_future *out,
+                                    hxc_run_stats *stats);
+
 /* ------------------------------------------------------------ tuning */
 
 /* Launch-shape and work-split knobs of the built-in kernels (the

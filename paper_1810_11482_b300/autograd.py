@@ -3,8 +3,9 @@
     uT = VarcoefHeat.apply(u0, kappa, c, steps, every)
 
 forward runs `steps` flux-form FTCS steps of u0 with diffusivity kappa on the
-library's kernels; backward runs the library's checkpointed discrete adjoint
-(states kept every `every` steps, 0 = ceil(sqrt(steps)), segments recomputed)
+library's kernels and keeps a checkpoint tape (the state every `every` steps,
+0 = ceil(sqrt(steps))); backward runs the library's discrete adjoint from that
+tape (each segment recomputed from its checkpoint, no second forward pass)
 seeded with the incoming gradient dL/du^T and returns dL/du0 and dL/dkappa.
 c = dt/h^2 is a fixed parameter.  Tensors must be contiguous float64 CUDA
 tensors of shape (ny, nx); PyTorch only provides their memory and the current
@@ -57,23 +58,26 @@ class VarcoefHeat(torch.autograd.Function):
         dev = _device()
         ny, nx = u0.shape
         uT = torch.empty_like(u0)
-        f, _ = hxc.varcoef_forward_run(dev, _wrap(dev, u0), _wrap(dev, kappa), ny, nx, float(c),
-                                       int(steps), _wrap(dev, uT), deps=[_after_torch(dev)])
+        tape = torch.empty((hxc.varcoef_tape_states(int(steps), int(every)), ny, nx),
+                           dtype=torch.float64, device=u0.device)
+        f, _ = hxc.varcoef_forward_tape(dev, _wrap(dev, u0), _wrap(dev, kappa), ny, nx, float(c),
+                                        int(steps), _wrap(dev, uT), _wrap(dev, tape),
+                                        every=int(every), deps=[_after_torch(dev)])
         _torch_waits(f)
-        ctx.save_for_backward(u0, kappa)
+        ctx.save_for_backward(tape, kappa)
         ctx.c, ctx.steps, ctx.every = float(c), int(steps), int(every)
         return uT
 
     @staticmethod
     def backward(ctx, grad_uT):
-        u0, kappa = ctx.saved_tensors
+        tape, kappa = ctx.saved_tensors
         dev = _device()
-        ny, nx = u0.shape
+        ny, nx = kappa.shape
         lamT = grad_uT.contiguous()
         gk = torch.empty_like(kappa)
-        gu = torch.empty_like(u0)
-        f, _ = hxc.varcoef_adjoint_run(dev, _wrap(dev, u0), _wrap(dev, kappa), _wrap(dev, lamT), ny,
-                                       nx, ctx.c, ctx.steps, _wrap(dev, gk), _wrap(dev, gu),
-                                       every=ctx.every, deps=[_after_torch(dev)])
+        gu = torch.empty_like(kappa)
+        f, _ = hxc.varcoef_adjoint_tape(dev, _wrap(dev, tape), _wrap(dev, kappa), _wrap(dev, lamT),
+                                        ny, nx, ctx.c, ctx.steps, _wrap(dev, gk), _wrap(dev, gu),
+                                        every=ctx.every, deps=[_after_torch(dev)])
         _torch_waits(f)
         return gu, gk, None, None, None

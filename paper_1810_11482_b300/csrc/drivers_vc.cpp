@@ -360,22 +360,38 @@ hxc_status hxc_varcoef_forward_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
     return HXC_OK;
 }
 
-hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh, hxc_buffer lTh,
-                                   int64_t ny, int64_t nx, double c, int steps, int every,
-                                   hxc_mode mode, hxc_buffer gkh, hxc_buffer gu0h, hxc_buffer uTh,
-                                   const hxc_future *deps, int ndeps, hxc_future *out,
-                                   hxc_run_stats *stats_out) {
+}  // extern "C"
+
+namespace {
+
+// The checkpointed adjoint.  With u0h it runs its own forward pass to lay
+// down the checkpoints; with tapeh (and no u0h, no uTh) it takes them from a
+// tape written by hxc_varcoef_forward_tape and starts with the segments.
+hxc_status adjoint_impl(hxc_device dh, hxc_buffer u0h, hxc_buffer tapeh, hxc_buffer kh,
+                        hxc_buffer lTh, int64_t ny, int64_t nx, double c, int steps, int every,
+                        hxc_mode mode, hxc_buffer gkh, hxc_buffer gu0h, hxc_buffer uTh,
+                        const hxc_future *deps, int ndeps, hxc_future *out,
+                        hxc_run_stats *stats_out) {
+    const char *fn = tapeh ? "hxc_varcoef_adjoint_tape" : "hxc_varcoef_adjoint_run";
     Ref<Device> d = dev_from_handle(dh);
-    if (!d || ny <= 0 || nx <= 0 || steps < 0 || every < 0 ||
+    if (!d || ny <= 0 || nx <= 0 || steps < 0 || every < 0 || (!u0h == !tapeh) ||
+        (tapeh && uTh) ||
         (mode != HXC_MODE_PLAIN && mode != HXC_MODE_GRAPH && mode != HXC_MODE_FUSED)) {
-        set_error("hxc_varcoef_adjoint_run: invalid arguments");
+        set_error("%s: invalid arguments", fn);
         return HXC_E_INVALID;
     }
     const int64_t n = ny * nx;
     const size_t nb = (size_t)n * 8;
-    Ref<Buffer> u0, kap, lT, gk, gu0, uT;
+    if (every == 0) every = std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, steps))));
+    const int nseg = steps > 0 ? (steps + every - 1) / every : 0;
+    Ref<Buffer> u0, tape, kap, lT, gk, gu0, uT;
     hxc_status st;
-    if ((st = need(u0, u0h, d.get(), nb, "adjoint.u0"))) return st;
+    if (tapeh) {
+        if ((st = need(tape, tapeh, d.get(), nb * std::max(1, nseg), "adjoint.tape"))) return st;
+        u0 = tape;  // state 0 is the tape's first checkpoint
+    } else if ((st = need(u0, u0h, d.get(), nb, "adjoint.u0"))) {
+        return st;
+    }
     if ((st = need(kap, kh, d.get(), nb, "adjoint.kappa"))) return st;
     if ((st = need(lT, lTh, d.get(), nb, "adjoint.lamT"))) return st;
     if ((st = need(gk, gkh, d.get(), nb, "adjoint.gk"))) return st;
@@ -387,11 +403,11 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
         for (auto o : outs)
             for (auto i : ins)
                 if (o && o == i) {
-                    set_error("hxc_varcoef_adjoint_run: an output aliases an input");
+                    set_error("%s: an output aliases an input", fn);
                     return HXC_E_INVALID;
                 }
         if (gk->ptr == gu0->ptr || (uT && (uT->ptr == gk->ptr || uT->ptr == gu0->ptr))) {
-            set_error("hxc_varcoef_adjoint_run: outputs alias");
+            set_error("%s: outputs alias", fn);
             return HXC_E_INVALID;
         }
     }
@@ -403,8 +419,8 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
         defer_run(dv,
                   [=](FutRef *ia, FutRef *ib) {
                       hxc_future h = nullptr;
-                      hxc_status s2 = hxc_varcoef_adjoint_run(dh, u0h, kh, lTh, ny, nx, c, steps, every, mode,
-                                                              gkh, gu0h, uTh, nullptr, 0, &h, nullptr);
+                      hxc_status s2 = adjoint_impl(dh, u0h, tapeh, kh, lTh, ny, nx, c, steps, every,
+                                                   mode, gkh, gu0h, uTh, nullptr, 0, &h, nullptr);
                       if (s2) return s2;
                       *ia = FutRef(reinterpret_cast<Future *>(h), true);
                       *ib = *ia;
@@ -418,16 +434,17 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
     Stats stats{stats_out};
     Device *dev = d.get();
     if ((st = dev->make_current())) return st;
-    if (every == 0) every = std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, steps))));
-    const int nseg = steps > 0 ? (steps + every - 1) / every : 0;
-    // scratch: coefficients, checkpoints 1..nseg-1, the segment store
+    // scratch: coefficients, checkpoints 1..nseg-1 (without a tape), the segment store
     // (states 1..every-1 of a segment), two work fields, two adjoint fields,
     // the per-face gradient sums
     void *pe, *ps, *pm, *pck, *pseg, *pw, *pl, *pf;
     if ((st = dev->scratch_get("adj.wE", nb, &pe))) return st;
     if ((st = dev->scratch_get("adj.wS", nb, &ps))) return st;
     if ((st = dev->scratch_get("adj.m", nb, &pm))) return st;
-    if ((st = dev->scratch_get("adj.ckpt", nb * std::max(1, nseg), &pck))) return st;
+    if (tape)
+        pck = tape->ptr;
+    else if ((st = dev->scratch_get("adj.ckpt", nb * std::max(1, nseg), &pck)))
+        return st;
     if ((st = dev->scratch_get("adj.seg", nb * std::max(1, every), &pseg))) return st;
     if ((st = dev->scratch_get("adj.work", nb * 2, &pw))) return st;
     if ((st = dev->scratch_get("adj.lam", nb * 2, &pl))) return st;
@@ -455,9 +472,10 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
         if ((s2 = op([=](cudaStream_t q) { return k::vc_coef(K, c, ny, nx, WE, WS, M, q); }))) return s2;
         sc.launch();
         // forward: states pass through the work fields; segment starts go to
-        // their checkpoint, the final state to uT (or a work field)
+        // their checkpoint, the final state to uT (or a work field); a tape
+        // holds the checkpoints already
         const double *cur = U0;
-        for (int t = 0; t < steps; t++) {
+        for (int t = 0; t < (tape ? 0 : steps); t++) {
             double *dst;
             if (t + 1 == steps)
                 dst = UT ? UT : WK + (size_t)((t + 1) & 1) * n;
@@ -534,7 +552,8 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
     if ((st = join_deps(dev, dv, &prev))) return st;
     FutRef last;
     if (mode == HXC_MODE_GRAPH) {
-        std::string key = key_of("adjoint", {(double)ny, (double)nx, c, (double)steps, (double)every},
+        std::string key = key_of(tape ? "adjoint_tape" : "adjoint",
+                                 {(double)ny, (double)nx, c, (double)steps, (double)every},
                                  {U0, K, LT, GK, GU, UT, WE, CK, SEG, WK, LM, FACE});
         Ref<Graph> g;
         auto capture = [&](int64_t *kernels) {
@@ -565,6 +584,137 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
                              AnyRef(gk.get(), false), AnyRef(gu0.get(), false)};
     if (uT) keep.push_back(AnyRef(uT.get(), false));
     if ((st = issue_device_op(dev, kJoinSlot, one(last), StreamOp(), keep, &fin))) return st;
+    if (out) *out = to_handle(fin);
+    return HXC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh, hxc_buffer lTh,
+                                   int64_t ny, int64_t nx, double c, int steps, int every,
+                                   hxc_mode mode, hxc_buffer gkh, hxc_buffer gu0h, hxc_buffer uTh,
+                                   const hxc_future *deps, int ndeps, hxc_future *out,
+                                   hxc_run_stats *stats_out) {
+    if (!u0h) {
+        set_error("hxc_varcoef_adjoint_run: u0 is NULL");
+        return HXC_E_INVALID;
+    }
+    return adjoint_impl(dh, u0h, nullptr, kh, lTh, ny, nx, c, steps, every, mode, gkh, gu0h, uTh,
+                        deps, ndeps, out, stats_out);
+}
+
+hxc_status hxc_varcoef_adjoint_tape(hxc_device dh, hxc_buffer tapeh, hxc_buffer kh, hxc_buffer lTh,
+                                    int64_t ny, int64_t nx, double c, int steps, int every,
+                                    hxc_mode mode, hxc_buffer gkh, hxc_buffer gu0h,
+                                    const hxc_future *deps, int ndeps, hxc_future *out,
+                                    hxc_run_stats *stats_out) {
+    if (!tapeh) {
+        set_error("hxc_varcoef_adjoint_tape: tape is NULL");
+        return HXC_E_INVALID;
+    }
+    return adjoint_impl(dh, nullptr, tapeh, kh, lTh, ny, nx, c, steps, every, mode, gkh, gu0h,
+                        nullptr, deps, ndeps, out, stats_out);
+}
+
+hxc_status hxc_varcoef_tape_states(int steps, int every, int64_t *states) {
+    if (steps < 0 || every < 0 || !states) {
+        set_error("hxc_varcoef_tape_states: invalid arguments");
+        return HXC_E_INVALID;
+    }
+    if (every == 0) every = std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, steps))));
+    *states = steps > 0 ? (steps + every - 1) / every : 1;
+    return HXC_OK;
+}
+
+hxc_status hxc_varcoef_forward_tape(hxc_device dh, hxc_buffer u0h, hxc_buffer kh, int64_t ny,
+                                    int64_t nx, double c, int steps, int every, hxc_buffer uTh,
+                                    hxc_buffer tapeh, const hxc_future *deps, int ndeps,
+                                    hxc_future *out, hxc_run_stats *stats_out) {
+    Ref<Device> d = dev_from_handle(dh);
+    if (!d || ny <= 0 || nx <= 0 || steps < 0 || every < 0) {
+        set_error("hxc_varcoef_forward_tape: invalid arguments");
+        return HXC_E_INVALID;
+    }
+    if (every == 0) every = std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, steps))));
+    const int nseg = steps > 0 ? (steps + every - 1) / every : 1;
+    const int64_t n = ny * nx;
+    const size_t nb = (size_t)n * 8;
+    Ref<Buffer> u0, kap, uT, tape;
+    hxc_status st;
+    if ((st = need(u0, u0h, d.get(), nb, "forward_tape.u0"))) return st;
+    if ((st = need(kap, kh, d.get(), nb, "forward_tape.kappa"))) return st;
+    if ((st = need(uT, uTh, d.get(), nb, "forward_tape.uT"))) return st;
+    if ((st = need(tape, tapeh, d.get(), nb * nseg, "forward_tape.tape"))) return st;
+    {
+        const char *t0 = (const char *)tape->ptr, *t1 = t0 + nb * nseg;
+        auto inside = [&](const void *p) { return (const char *)p + nb > t0 && (const char *)p < t1; };
+        if (uT->ptr == kap->ptr || uT->ptr == u0->ptr || inside(u0->ptr) || inside(kap->ptr) ||
+            inside(uT->ptr)) {
+            set_error("hxc_varcoef_forward_tape: uT, the tape and the inputs must not overlap");
+            return HXC_E_INVALID;
+        }
+    }
+    std::vector<FutRef> dv;
+    if ((st = deps_from_handles(deps, ndeps, &dv))) return st;
+    if (stats_out) memset(stats_out, 0, sizeof *stats_out);
+    Stats stats{stats_out};
+    Device *dev = d.get();
+    if ((st = dev->make_current())) return st;
+    void *pw, *pe, *ps, *pm;
+    if ((st = dev->scratch_get("fwdt.work", nb * 2, &pw))) return st;
+    if ((st = dev->scratch_get("fwd.wE", nb, &pe))) return st;
+    if ((st = dev->scratch_get("fwd.wS", nb, &ps))) return st;
+    if ((st = dev->scratch_get("fwd.m", nb, &pm))) return st;
+    double *WK = (double *)pw, *WE = (double *)pe, *WS = (double *)ps, *M = (double *)pm;
+    const double *K = (const double *)kap->ptr, *U0 = (const double *)u0->ptr;
+    double *UT = (double *)uT->ptr, *TP = (double *)tape->ptr;
+    FutRef f;
+    if ((st = join_deps(dev, dv, &f))) return st;
+    auto op = [&](StreamOp o) -> hxc_status {
+        FutRef g;
+        hxc_status s3 = issue_device_op(dev, 0, one(f), std::move(o), {}, &g);
+        if (!s3) f = g;
+        return s3;
+    };
+    if ((st = op([=](cudaStream_t q) {
+             cudaError_t e = cudaMemcpyAsync(TP, U0, nb, cudaMemcpyDeviceToDevice, q);
+             if (e == cudaSuccess) e = k::vc_coef(K, c, ny, nx, WE, WS, M, q);
+             return e;
+         })))
+        return st;
+    stats.launch();
+    // the same sequence of states as the adjoint run's own forward pass:
+    // segment starts into the tape, the final state into uT, the others
+    // through two work fields
+    const double *cur = TP;
+    for (int t = 0; t < steps; t++) {
+        double *dst;
+        if (t + 1 == steps)
+            dst = UT;
+        else if ((t + 1) % every == 0)
+            dst = TP + (size_t)((t + 1) / every) * n;
+        else
+            dst = WK + (size_t)((t + 1) & 1) * n;
+        if (dst == cur) dst = WK + (size_t)(((t + 1) & 1) ^ 1) * n;
+        const double *src = cur;
+        if ((st = op([=](cudaStream_t q) { return k::vc_step(src, dst, WE, WS, M, ny, nx, q); })))
+            return st;
+        stats.launch();
+        cur = dst;
+    }
+    if (steps == 0 &&
+        (st = op([=](cudaStream_t q) {
+             return cudaMemcpyAsync(UT, U0, nb, cudaMemcpyDeviceToDevice, q);
+         })))
+        return st;
+    FutRef fin;
+    if ((st = issue_device_op(dev, kJoinSlot, one(f), StreamOp(),
+                              {AnyRef(u0.get(), false), AnyRef(kap.get(), false),
+                               AnyRef(uT.get(), false), AnyRef(tape.get(), false)},
+                              &fin)))
+        return st;
     if (out) *out = to_handle(fin);
     return HXC_OK;
 }

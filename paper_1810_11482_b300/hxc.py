@@ -217,6 +217,15 @@ _SIGS = {
     "hxc_varcoef_forward_run": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double,
                                        ctypes.c_int, c_buf, ctypes.POINTER(c_fut), ctypes.c_int,
                                        ctypes.POINTER(c_fut), ctypes.POINTER(hxc_run_stats)]),
+    "hxc_varcoef_tape_states": (c_st, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(i64)]),
+    "hxc_varcoef_forward_tape": (c_st, [c_dev, c_buf, c_buf, i64, i64, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int, c_buf, c_buf, ctypes.POINTER(c_fut),
+                                        ctypes.c_int, ctypes.POINTER(c_fut),
+                                        ctypes.POINTER(hxc_run_stats)]),
+    "hxc_varcoef_adjoint_tape": (c_st, [c_dev, c_buf, c_buf, c_buf, i64, i64, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, c_buf, c_buf,
+                                        ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut),
+                                        ctypes.POINTER(hxc_run_stats)]),
     "hxc_host_norms": (c_st, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(i64), ctypes.c_int,
                               ctypes.c_void_p]),
     "hxc_heat2d_stream_run": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, i64, i64, i64,
@@ -571,6 +580,33 @@ def varcoef_adjoint_run(dev, u0, kappa, lamT, ny, nx, c, steps, gk, gu0, uT=None
                                         MODES[mode], gk.h, gu0.h, uT.h if uT is not None else None,
                                         arr, nd, ctypes.byref(out), ctypes.byref(st)),
           "varcoef_adjoint_run")
+    return Future(out.value), st
+
+
+def varcoef_tape_states(steps, every=0):
+    v = i64()
+    check(lib().hxc_varcoef_tape_states(steps, every, ctypes.byref(v)), "varcoef_tape_states")
+    return int(v.value)
+
+
+def varcoef_forward_tape(dev, u0, kappa, ny, nx, c, steps, uT, tape, every=0, deps=()):
+    arr, nd = _futs(deps)
+    out = c_fut()
+    st = hxc_run_stats()
+    check(lib().hxc_varcoef_forward_tape(dev.h, u0.h, kappa.h, ny, nx, c, steps, every, uT.h,
+                                         tape.h, arr, nd, ctypes.byref(out), ctypes.byref(st)),
+          "varcoef_forward_tape")
+    return Future(out.value), st
+
+
+def varcoef_adjoint_tape(dev, tape, kappa, lamT, ny, nx, c, steps, gk, gu0, every=0,
+                         mode="fused", deps=()):
+    arr, nd = _futs(deps)
+    out = c_fut()
+    st = hxc_run_stats()
+    check(lib().hxc_varcoef_adjoint_tape(dev.h, tape.h, kappa.h, lamT.h, ny, nx, c, steps, every,
+                                         MODES[mode], gk.h, gu0.h, arr, nd, ctypes.byref(out),
+                                         ctypes.byref(st)), "varcoef_adjoint_tape")
     return Future(out.value), st
 
 

@@ -164,6 +164,48 @@ def test_adjoint_small_vs_oracle_and_schedules(dev):
             assert np.array_equal(gk, ref[0]) and np.array_equal(gu, ref[1]), (every, mode)
 
 
+def test_checkpoint_tape_matches_adjoint_run(dev):
+    """A forward run that keeps its checkpoints (hxc_varcoef_forward_tape)
+    gives the forward run's final state and, as checkpoint k, the state after
+    k * every steps; the adjoint from that tape gives the bits of the adjoint
+    run that does its own forward pass, for every checkpoint interval and
+    mode; a tape that is too small is rejected."""
+    ny, nx, c = 18, 13, 0.15
+    kap = synth.uniform(423, ny * nx, lo=0.5, hi=1.5).reshape(ny, nx)
+    u0 = synth.uniform(424, ny * nx).reshape(ny, nx)
+    lamT = synth.uniform(427, ny * nx, lo=-1, hi=1).reshape(ny, nx)
+    bu, bk, bl = up(dev, u0), up(dev, kap), up(dev, lamT)
+    for steps in (0, 1, 7, 10):
+        want_uT = dev.buffer(u0.nbytes)
+        hxc.varcoef_forward_run(dev, bu, bk, ny, nx, c, steps, want_uT)[0].get()
+        want_uT = down(want_uT, u0.shape)
+        for every in (0, 1, 2, 3, 7, 9):
+            ns = hxc.varcoef_tape_states(steps, every)
+            e = every or max(1, int(np.ceil(np.sqrt(max(1, steps)))))
+            assert ns == (max(1, -(-steps // e)) if steps else 1)
+            tape, uT = dev.buffer(ns * u0.nbytes), dev.buffer(u0.nbytes)
+            hxc.varcoef_forward_tape(dev, bu, bk, ny, nx, c, steps, uT, tape, every)[0].get()
+            assert np.array_equal(down(uT, u0.shape), want_uT), (steps, every)
+            tp = down(tape, (ns, ny, nx))
+            for kk in range(ns):
+                ref = dev.buffer(u0.nbytes)
+                hxc.varcoef_forward_run(dev, bu, bk, ny, nx, c, kk * e, ref)[0].get()
+                assert np.array_equal(tp[kk], down(ref, u0.shape)), (steps, every, kk)
+            for mode in ("plain", "graph", "fused"):
+                gk, gu, _, _ = adjoint(dev, u0, kap, lamT, c, steps, every, mode)
+                tk, tu = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+                hxc.varcoef_adjoint_tape(dev, tape, bk, bl, ny, nx, c, steps, tk, tu, every,
+                                         mode)[0].get()
+                assert np.array_equal(down(tk, u0.shape), gk), (steps, every, mode)
+                assert np.array_equal(down(tu, u0.shape), gu), (steps, every, mode)
+    small = dev.buffer(u0.nbytes)
+    with pytest.raises(hxc.HxcError):
+        hxc.varcoef_forward_tape(dev, bu, bk, ny, nx, c, 10, dev.buffer(u0.nbytes), small, 3)
+    with pytest.raises(hxc.HxcError):
+        hxc.varcoef_adjoint_tape(dev, small, bk, bl, ny, nx, c, 10, dev.buffer(u0.nbytes),
+                                 dev.buffer(u0.nbytes), 3)
+
+
 def test_adjoint_zero_steps(dev):
     u0 = synth.uniform(425, 30).reshape(5, 6)
     kap = np.ones((5, 6))
@@ -228,6 +270,14 @@ def test_adjoint_full_config_properties(dev):
     gk2, gu2 = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
     hxc.varcoef_adjoint_run(dev, bu0, bk, lam, n, n, c, steps, gk2, gu2, None, 1, "fused")[0].get()
     assert np.array_equal(down(gk2, u0.shape), gk_h) and np.array_equal(down(gu2, u0.shape), gu_h)
+    # the training-step form: forward with a checkpoint tape, adjoint from it
+    tape = dev.buffer(hxc.varcoef_tape_states(steps) * u0.nbytes)
+    uT2, gk3, gu3 = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    hxc.varcoef_forward_tape(dev, bu0, bk, n, n, c, steps, uT2, tape)[0].get()
+    assert np.array_equal(down(uT2, u0.shape), down(uT, u0.shape))
+    hxc.varcoef_adjoint_tape(dev, tape, bk, lam, n, n, c, steps, gk3, gu3)[0].get()
+    assert np.array_equal(down(gk3, u0.shape), gk_h) and np.array_equal(down(gu3, u0.shape), gu_h)
+    del tape, uT2, gk3, gu3
     # dL/du0 = A^steps lambda^T (symmetric step matrix, same kernel)
     fw = dev.buffer(u0.nbytes)
     hxc.varcoef_forward_run(dev, lam, bk, n, n, c, steps, fw)[0].get()
