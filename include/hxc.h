@@ -617,22 +617,22 @@ hxc_status hxc_varcoef_adjoint_tape(hxc_device dev, hxc_buffer tape, hxc_buffer 
  *   "heat2d.rows"  rows each warp of the 2D kernel walks (default 16).
  *   "heat2d.occupancy"  minimum resident 256-thread CTAs per SM the 2D
  *                  kernel is compiled for, 4..6 (default 4).
- *   "heat3d.zchunks"  z chunks of a 3D launch of forms 0..2, 0 = fill whole
+ *   "heat3d.zchunks"  z chunks of a 3D launch of form 2, 0 = fill whole
  *                  waves.
- *   "heat3d.variant"  3D kernel form: 0 = plane registers copied each z
- *                  step, 1 = plane registers rotated (z loop unrolled by 3),
- *                  2 = rotated, arithmetic on paired FP32 instructions,
- *                  3 = two plane registers per level (centre + partial sum),
- *                  2 x 4 cells per thread, 64 x 64 regions, the z range split
+ *   "heat3d.variant"  3D kernel form: 2 = three plane registers per level
+ *                  (rotated, z loop unrolled by 3), arithmetic on paired FP32
+ *                  instructions, 64 x 32 regions, z cut into chunks (also
+ *                  the form for planes of more than 2^32 cells), 3 = two
+ *                  plane registers per level (centre + partial sum), 2 x 4
+ *                  cells per thread, 64 x 64 regions, the z range split
  *                  evenly over one CTA per SM, 4 = form 3 with the input
- *                  planes copied into a shared-memory ring two planes ahead
- *                  (default), 6 = form 4 with packed narrow tiles (the
- *                  columns and rows left over by the 64 - 2T wide output
- *                  tiles go to 16-wide regions run four or sixteen to a CTA
- *                  in lane segments and warp groups).  Forms 3, 4 and 6
- *                  launched with an hxc_launch_cfg take 512 threads per CTA
- *                  and any grid (form 6 at least 2 CTAs when it has both
- *                  kinds of tiles).
+ *                  planes copied into a shared-memory ring two planes ahead,
+ *                  6 = form 4 with packed narrow tiles (the columns and rows
+ *                  left over by the 64 - 2T wide output tiles go to 16-wide
+ *                  regions run four or sixteen to a CTA in lane segments and
+ *                  warp groups; the default).  Forms 3, 4 and 6 launched with
+ *                  an hxc_launch_cfg take 512 threads per CTA and any grid
+ *                  (form 6 at least 2 CTAs when it has both kinds of tiles).
  *   "heat3d.variant1"  the form used for one-step launches (PLAIN mode and
  *                  single-step remainders), the values above plus 5 = a
  *                  streaming kernel (4 adjacent x cells per thread, 16-byte

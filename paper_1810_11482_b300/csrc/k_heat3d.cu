@@ -1,22 +1,23 @@
 // 3D 7-point FTCS, FP32, periodic, T (1..4) fused steps per launch.
 //
-// Canonical arithmetic (every variant, every T):
+// Canonical arithmetic (every form, every T):
 //   s  = (((u[x-1] + u[x+1]) + (u[y-1] + u[y+1])) + u[z-1]) + u[z+1]
 //   t  = fma(-6, u, s);   u' = fma(r, t, u)            (FP32, round-to-nearest)
 // so T fused steps give the same bits as T single-step launches.
 //
-// Temporal blocking.  A CTA owns an x-y region of RX x RY = 64 x 32 columns
-// (its output tile plus a halo of T columns on every side) and streams it
-// along z.  Level t (the field after t steps) is kept per thread in
-// registers for three consecutive planes (z-1, z, z+1) of the 2 x 2 columns
-// the thread owns; x-neighbours come from the adjacent lanes by shuffles and
-// y-neighbours from a shared-memory copy of the level's middle plane.  In
-// every iteration a new level-0 plane is loaded and each level t < T
-// produces one plane of level t+1; the levels advance together (their
-// inputs are the registers and shared planes at the start of the
-// iteration), so level t runs 2t planes behind level 0.  Cells within
-// distance t of the region edge are wrong at level t and are never written:
-// only the central (RX-2T) x (RY-2T) columns of level T are stored.
+// Temporal blocking.  A CTA owns an x-y region (its output tile plus a halo
+// of T columns on every side) and streams it along z.  Level t (the field
+// after t steps) is kept per thread in registers for the columns the thread
+// owns; x-neighbours come from the adjacent lanes by shuffles and
+// y-neighbours from the thread's own rows or from shared memory.  In every
+// iteration a new level-0 plane arrives and each level t < T produces one
+// plane of level t+1.  Cells within distance t of the region edge are wrong
+// at level t and are never written: only the central columns of level T are
+// stored.  Forms: 2 (three plane registers per level, 64 x 32 regions, z cut
+// into chunks), 3 (two registers per level, 64 x 64 regions, the (region,
+// plane) pairs split evenly over one CTA per SM), 4 (form 3 fed by a
+// cp.async ring of input planes), 6 (form 4 with packed narrow tiles), and
+// for one-step launches 5 (a streaming kernel).
 #include <algorithm>
 
 #include "f32x2.cuh"
@@ -29,136 +30,14 @@ namespace k {
 namespace {
 constexpr int RX = 64, RY = 32, NT = 512;
 
-__device__ __forceinline__ float ftcs7(float u, float xm, float xp, float ym, float yp, float zm,
-                                       float zp, float r) {
-    float s = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), zm), zp);
-    float t = __fmaf_rn(-6.0f, u, s);
-    return __fmaf_rn(r, t, u);
-}
-
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
 }
 }  // namespace
 
-template <int T>
-__global__ void __launch_bounds__(NT, 1)
-    k_heat3d_tb(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
-                float r, int zchunk) {
-    constexpr int BX = RX - 2 * T, BY = RY - 2 * T;
-    __shared__ __align__(16) float S[T][RY][RX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tiles_x = (nx + BX - 1) / BX, tiles_y = (ny + BY - 1) / BY;
-    const int nchunks = (nz + zchunk - 1) / zchunk;
-    const int nblk = tiles_x * tiles_y * nchunks;
-    const int rx = 2 * lane, ry = 2 * warp;
-    // rows of the neighbouring warps (clamped inside the region: the clamped
-    // rows only feed cells that are never stored)
-    const int ryu = ry > 0 ? ry - 1 : 0, ryd = ry + 2 < RY ? ry + 2 : RY - 1;
-
-    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-        const int tx = b % tiles_x, ty = (b / tiles_x) % tiles_y, ch = b / (tiles_x * tiles_y);
-        const int x0 = tx * BX - T, y0 = ty * BY - T;
-        const int z0 = ch * zchunk, z1 = min(nz, z0 + zchunk);
-        const int gx0 = wrapi(x0 + rx, nx), gx1 = wrapi(x0 + rx + 1, nx);
-        const int gy0 = wrapi(y0 + ry, ny), gy1 = wrapi(y0 + ry + 1, ny);
-        // output columns of this thread (inside the tile and the field)
-        const bool ox0 = rx >= T && rx < RX - T && x0 + rx < nx;
-        const bool ox1 = rx + 1 >= T && rx + 1 < RX - T && x0 + rx + 1 < nx;
-        const bool oy0 = ry >= T && ry < RY - T && y0 + ry < ny;
-        const bool oy1 = ry + 1 >= T && ry + 1 < RY - T && y0 + ry + 1 < ny;
-        const size_t o00 = (size_t)gy0 * nx + gx0, o01 = (size_t)gy0 * nx + gx1;
-        const size_t o10 = (size_t)gy1 * nx + gx0, o11 = (size_t)gy1 * nx + gx1;
-        const size_t plane = (size_t)ny * nx;
-
-        // level t planes: P = newest-2, M = newest-1, N = newest  (4 columns each)
-        float P[T][4], M[T][4], N[T][4];
-#pragma unroll
-        for (int t = 0; t < T; t++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) P[t][c] = M[t][c] = N[t][c] = 0.f;
-
-        const int iters = (z1 - z0) + 3 * T - 1;
-        // prefetch the first level-0 plane
-        float nxt[4];
-        {
-            const size_t zo = (size_t)wrapi(z0 - T, nz) * plane;
-            nxt[0] = __ldg(src + zo + o00);
-            nxt[1] = __ldg(src + zo + o01);
-            nxt[2] = __ldg(src + zo + o10);
-            nxt[3] = __ldg(src + zo + o11);
-        }
-        for (int i = 0; i < iters; i++) {
-            // level 0: shift in the loaded plane, prefetch the next one
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                P[0][c] = M[0][c];
-                M[0][c] = N[0][c];
-                N[0][c] = nxt[c];
-            }
-            if (i + 1 < iters) {
-                const size_t zo = (size_t)wrapi(z0 - T + i + 1, nz) * plane;
-                nxt[0] = __ldg(src + zo + o00);
-                nxt[1] = __ldg(src + zo + o01);
-                nxt[2] = __ldg(src + zo + o10);
-                nxt[3] = __ldg(src + zo + o11);
-            }
-            *reinterpret_cast<float2 *>(&S[0][ry][rx]) = make_float2(M[0][0], M[0][1]);
-            *reinterpret_cast<float2 *>(&S[0][ry + 1][rx]) = make_float2(M[0][2], M[0][3]);
-            __syncthreads();
-            // every level t produces level t+1 at the plane of M[t]
-            float V[T][4];
-#pragma unroll
-            for (int t = 0; t < T; t++) {
-                const float2 up = *reinterpret_cast<const float2 *>(&S[t][ryu][rx]);
-                const float2 dn = *reinterpret_cast<const float2 *>(&S[t][ryd][rx]);
-                const float l0 = __shfl_up_sync(0xffffffffu, M[t][1], 1);
-                const float r0 = __shfl_down_sync(0xffffffffu, M[t][0], 1);
-                const float l1 = __shfl_up_sync(0xffffffffu, M[t][3], 1);
-                const float r1 = __shfl_down_sync(0xffffffffu, M[t][2], 1);
-                V[t][0] = ftcs7(M[t][0], l0, M[t][1], up.x, M[t][2], P[t][0], N[t][0], r);
-                V[t][1] = ftcs7(M[t][1], M[t][0], r0, up.y, M[t][3], P[t][1], N[t][1], r);
-                V[t][2] = ftcs7(M[t][2], l1, M[t][3], M[t][0], dn.x, P[t][2], N[t][2], r);
-                V[t][3] = ftcs7(M[t][3], M[t][2], r1, M[t][1], dn.y, P[t][3], N[t][3], r);
-            }
-            __syncthreads();
-            // levels 1..T-1 shift in their new plane and publish the middle one
-#pragma unroll
-            for (int t = 1; t < T; t++) {
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    P[t][c] = M[t][c];
-                    M[t][c] = N[t][c];
-                    N[t][c] = V[t - 1][c];
-                }
-                *reinterpret_cast<float2 *>(&S[t][ry][rx]) = make_float2(M[t][0], M[t][1]);
-                *reinterpret_cast<float2 *>(&S[t][ry + 1][rx]) = make_float2(M[t][2], M[t][3]);
-            }
-            // level T: V[T-1] is the output plane z0 + i - 3T + 1
-            const int zout = z0 + i - 3 * T + 1;
-            if (zout >= z0 && zout < z1) {
-                float *d = dst + (size_t)zout * plane;
-                if (oy0 && ox0) d[o00] = V[T - 1][0];
-                if (oy0 && ox1) d[o01] = V[T - 1][1];
-                if (oy1 && ox0) d[o10] = V[T - 1][2];
-                if (oy1 && ox1) d[o11] = V[T - 1][3];
-            }
-        }
-        __syncthreads();  // the shared planes are reused by the next block item
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Variant 1: the same data flow and arithmetic as k_heat3d_tb, with the
-// three plane slots of every level rotated instead of copied.  Slot roles
-// (oldest, middle, newest) advance by one each iteration, so the z loop is
-// unrolled by three and every register index is a compile-time constant;
-// levels are computed top-down so that level t writes its output plane
-// straight into the oldest slot of level t+1 (which level t+1 has already
-// consumed in this iteration).  Level-0 planes are loaded as float2 where
-// the thread's two columns are adjacent in memory, and the z index of the
-// next plane is advanced without a division.
+// Global offsets of a thread's 2 x 2 cells (form 2).
 namespace {
 
 struct Cols {
@@ -166,159 +45,19 @@ struct Cols {
     bool pair;  // columns 0/1 (and 2/3) adjacent and 8-byte aligned
 };
 
-__device__ __forceinline__ void load4(float (&v)[4], const float *__restrict__ src, size_t zo,
-                                      const Cols &c) {
-    if (c.pair) {
-        const float2 a = __ldg(reinterpret_cast<const float2 *>(src + zo + c.o00));
-        const float2 b = __ldg(reinterpret_cast<const float2 *>(src + zo + c.o10));
-        v[0] = a.x;
-        v[1] = a.y;
-        v[2] = b.x;
-        v[3] = b.y;
-    } else {
-        v[0] = __ldg(src + zo + c.o00);
-        v[1] = __ldg(src + zo + c.o01);
-        v[2] = __ldg(src + zo + c.o10);
-        v[3] = __ldg(src + zo + c.o11);
-    }
-}
-
-// One z iteration with rotation R (slot R holds each level's oldest plane
-// when the iteration starts).  Returns nothing; writes the level-T plane.
-template <int T, int R>
-__device__ __forceinline__ void h3_iter(float (&L)[T][3][4], float (&nxt)[4],
-                                        float (*S)[RY][RX], const float *__restrict__ src,
-                                        float *__restrict__ dst, const Cols &c, int rx, int ry,
-                                        int ryu, int ryd, int &zl, int nz, size_t plane, bool more,
-                                        int zout, int z0, int z1, bool ox0, bool ox1, bool oy0,
-                                        bool oy1, float r) {
-    constexpr int P = R % 3, M = (R + 1) % 3, N = (R + 2) % 3;
-    // level 0 takes the prefetched plane into its oldest slot: roles become
-    // (M, N, P) for level 0 in this iteration
-#pragma unroll
-    for (int q = 0; q < 4; q++) L[0][P][q] = nxt[q];
-    if (more) {
-        zl = zl + 1 < nz ? zl + 1 : zl + 1 - nz;
-        load4(nxt, src, (size_t)zl * plane, c);
-    }
-    *reinterpret_cast<float2 *>(&S[0][ry][rx]) = make_float2(L[0][N][0], L[0][N][1]);
-    *reinterpret_cast<float2 *>(&S[0][ry + 1][rx]) = make_float2(L[0][N][2], L[0][N][3]);
-    __syncthreads();
-    float out[4];
-#pragma unroll
-    for (int t = T - 1; t >= 0; t--) {
-        // roles of level t: oldest a, middle b, newest d
-        const int a = t == 0 ? M : P, b = t == 0 ? N : M, d = t == 0 ? P : N;
-        const float2 up = *reinterpret_cast<const float2 *>(&S[t][ryu][rx]);
-        const float2 dn = *reinterpret_cast<const float2 *>(&S[t][ryd][rx]);
-        const float l0 = __shfl_up_sync(0xffffffffu, L[t][b][1], 1);
-        const float r0 = __shfl_down_sync(0xffffffffu, L[t][b][0], 1);
-        const float l1 = __shfl_up_sync(0xffffffffu, L[t][b][3], 1);
-        const float r1 = __shfl_down_sync(0xffffffffu, L[t][b][2], 1);
-        float v0 = ftcs7(L[t][b][0], l0, L[t][b][1], up.x, L[t][b][2], L[t][a][0], L[t][d][0], r);
-        float v1 = ftcs7(L[t][b][1], L[t][b][0], r0, up.y, L[t][b][3], L[t][a][1], L[t][d][1], r);
-        float v2 = ftcs7(L[t][b][2], l1, L[t][b][3], L[t][b][0], dn.x, L[t][a][2], L[t][d][2], r);
-        float v3 = ftcs7(L[t][b][3], L[t][b][2], r1, L[t][b][1], dn.y, L[t][a][3], L[t][d][3], r);
-        if (t == T - 1) {
-            out[0] = v0;
-            out[1] = v1;
-            out[2] = v2;
-            out[3] = v3;
-        } else {
-            // level t+1 (computed above) no longer needs its oldest slot P
-            L[t + 1][P][0] = v0;
-            L[t + 1][P][1] = v1;
-            L[t + 1][P][2] = v2;
-            L[t + 1][P][3] = v3;
-        }
-    }
-    __syncthreads();
-    // levels 1..T-1 now hold (M, N, P) as (oldest, middle, newest): publish the middle
-#pragma unroll
-    for (int t = 1; t < T; t++) {
-        *reinterpret_cast<float2 *>(&S[t][ry][rx]) = make_float2(L[t][N][0], L[t][N][1]);
-        *reinterpret_cast<float2 *>(&S[t][ry + 1][rx]) = make_float2(L[t][N][2], L[t][N][3]);
-    }
-    if (zout >= z0 && zout < z1) {
-        float *d = dst + (size_t)zout * plane;
-        if (c.pair && ox0 && ox1) {
-            if (oy0) *reinterpret_cast<float2 *>(d + c.o00) = make_float2(out[0], out[1]);
-            if (oy1) *reinterpret_cast<float2 *>(d + c.o10) = make_float2(out[2], out[3]);
-        } else {
-            if (oy0 && ox0) d[c.o00] = out[0];
-            if (oy0 && ox1) d[c.o01] = out[1];
-            if (oy1 && ox0) d[c.o10] = out[2];
-            if (oy1 && ox1) d[c.o11] = out[3];
-        }
-    }
-}
-
 }  // namespace
 
-template <int T>
-__global__ void __launch_bounds__(NT, 1)
-    k_heat3d_rot(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
-                 float r, int zchunk) {
-    constexpr int BX = RX - 2 * T, BY = RY - 2 * T;
-    __shared__ __align__(16) float S[T][RY][RX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tiles_x = (nx + BX - 1) / BX, tiles_y = (ny + BY - 1) / BY;
-    const int nchunks = (nz + zchunk - 1) / zchunk;
-    const int nblk = tiles_x * tiles_y * nchunks;
-    const int rx = 2 * lane, ry = 2 * warp;
-    const int ryu = ry > 0 ? ry - 1 : 0, ryd = ry + 2 < RY ? ry + 2 : RY - 1;
-    const size_t plane = (size_t)ny * nx;
-
-    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-        const int tx = b % tiles_x, ty = (b / tiles_x) % tiles_y, ch = b / (tiles_x * tiles_y);
-        const int x0 = tx * BX - T, y0 = ty * BY - T;
-        const int z0 = ch * zchunk, z1 = min(nz, z0 + zchunk);
-        const int gx0 = wrapi(x0 + rx, nx), gx1 = wrapi(x0 + rx + 1, nx);
-        const int gy0 = wrapi(y0 + ry, ny), gy1 = wrapi(y0 + ry + 1, ny);
-        const bool ox0 = rx >= T && rx < RX - T && x0 + rx < nx;
-        const bool ox1 = rx + 1 >= T && rx + 1 < RX - T && x0 + rx + 1 < nx;
-        const bool oy0 = ry >= T && ry < RY - T && y0 + ry < ny;
-        const bool oy1 = ry + 1 >= T && ry + 1 < RY - T && y0 + ry + 1 < ny;
-        Cols c;
-        c.o00 = (size_t)gy0 * nx + gx0;
-        c.o01 = (size_t)gy0 * nx + gx1;
-        c.o10 = (size_t)gy1 * nx + gx0;
-        c.o11 = (size_t)gy1 * nx + gx1;
-        c.pair = gx1 == gx0 + 1 && (gx0 & 1) == 0 && (nx & 1) == 0;
-
-        float L[T][3][4];
-#pragma unroll
-        for (int t = 0; t < T; t++)
-#pragma unroll
-            for (int s = 0; s < 3; s++)
-#pragma unroll
-                for (int q = 0; q < 4; q++) L[t][s][q] = 0.f;
-
-        const int iters = (z1 - z0) + 3 * T - 1;
-        int zl = wrapi(z0 - T, nz);  // z of the plane in nxt
-        float nxt[4];
-        load4(nxt, src, (size_t)zl * plane, c);
-        int zout = z0 - 3 * T + 1;  // output plane of iteration i: zout + i
-        for (int i = 0; i < iters; i += 3) {
-            h3_iter<T, 0>(L, nxt, S, src, dst, c, rx, ry, ryu, ryd, zl, nz, plane, i + 1 < iters,
-                          zout + i, z0, z1, ox0, ox1, oy0, oy1, r);
-            if (i + 1 >= iters) break;
-            h3_iter<T, 1>(L, nxt, S, src, dst, c, rx, ry, ryu, ryd, zl, nz, plane, i + 2 < iters,
-                          zout + i + 1, z0, z1, ox0, ox1, oy0, oy1, r);
-            if (i + 2 >= iters) break;
-            h3_iter<T, 2>(L, nxt, S, src, dst, c, rx, ry, ryu, ryd, zl, nz, plane, i + 3 < iters,
-                          zout + i + 2, z0, z1, ox0, ox1, oy0, oy1, r);
-        }
-        __syncthreads();  // the shared planes are reused by the next block item
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Variant 2: variant 1 with the arithmetic on packed pairs.  The two
-// x-adjacent cells of each of the thread's rows are held as one 64-bit pair
-// (the low half the lower x) and updated with the paired FP32 instructions
-// (f32x2.cuh): the canonical expression, evaluated on two cells per
-// instruction.
+// Form 2.  A CTA owns a 64 x 32 region, a thread 2 x 2 cells: the two
+// x-adjacent cells of each of its rows held as one 64-bit pair (the low half
+// the lower x) and updated with the paired FP32 instructions (f32x2.cuh).
+// Each level keeps three plane slots (oldest, middle, newest) whose roles
+// rotate by one each iteration (the z loop is unrolled by three, so every
+// register index is a compile-time constant); levels are computed top-down,
+// level t writing its output plane straight into the oldest slot of level
+// t+1, so level t runs 3t-1 planes behind level 0.  y-neighbours outside the
+// thread's two rows come from a shared-memory copy of each level's middle
+// plane.
 namespace {
 
 // ftcs7 on two cells at once (same operation order and rounding)
@@ -932,7 +671,6 @@ template <int T, int SW>
 __device__ __forceinline__ void v6_units_run(const float *__restrict__ src, float *__restrict__ dst,
                                              int nz, int ny, int nx, float r, const Tiling3 &tl,
                                              int64_t w0, int64_t w1) {
-    constexpr int FW = 64 - 2 * T, NWD = 16 - 2 * T;
     extern __shared__ __align__(16) f2 v4_smem[];
     f2 *ring = v4_smem;
     f2 *sbase = v4_smem + (size_t)V4_RS * V3_H * 32;
@@ -1218,29 +956,11 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
         }
     }
     if (cfg && cfg->block[0] * cfg->block[1] * cfg->block[2] != NT) return cudaErrorInvalidValue;
-    if (variant >= 2) {
-        switch (steps) {
-            case 1: k_heat3d_pk<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-            case 2: k_heat3d_pk<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-            case 3: k_heat3d_pk<3><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-            case 4: k_heat3d_pk<4><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-        }
-        return cudaGetLastError();
-    }
-    if (variant == 1) {
-        switch (steps) {
-            case 1: k_heat3d_rot<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-            case 2: k_heat3d_rot<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-            case 3: k_heat3d_rot<3><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-            case 4: k_heat3d_rot<4><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-        }
-        return cudaGetLastError();
-    }
     switch (steps) {
-        case 1: k_heat3d_tb<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-        case 2: k_heat3d_tb<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-        case 3: k_heat3d_tb<3><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
-        case 4: k_heat3d_tb<4><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        case 1: k_heat3d_pk<1><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        case 2: k_heat3d_pk<2><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        case 3: k_heat3d_pk<3><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
+        case 4: k_heat3d_pk<4><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
     }
     return cudaGetLastError();
 }

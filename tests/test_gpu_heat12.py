@@ -283,11 +283,11 @@ def test_heat2d_device_norms_when_the_tile_count_changes(dev):
 
 def test_heat2d_full_config(dev):
     """8192^2, 64 tiles of 1024^2, r = 0.2, 1000 steps, snapshots every 100
-    steps: every mode bit-identical; a corner window checked against the
-    oracle (the dependence cone of a cell after 1000 steps is 1000 cells
-    wide, so cells 1000 away from the window's cut edges are exact); device
-    norms against host norms; the last snapshot's norms against norms of the
-    downloaded final field."""
+    steps: every mode bit-identical; the whole field against the oracle, and
+    a corner window against the oracle's windowed run (the dependence cone of
+    a cell after 1000 steps is 1000 cells wide, so cells 1000 away from the
+    window's cut edges are exact); device norms against host norms; the last
+    snapshot's norms against norms of the downloaded final field."""
     n, steps, r, every = 8192, 1000, 0.2, 100
     u0 = synth.bumps2d(n, n, seed=2)
     outs = {}
@@ -301,6 +301,12 @@ def test_heat2d_full_config(dev):
     scale = np.max(np.abs(got))
     w = oracle.heat2d_window(u0, n - 1300, n - 1300, 1300, 1300, r, steps)
     assert np.max(np.abs(got[n - 300:, n - 300:] - w[1000:, 1000:])) <= TOL * scale
+    # the whole field against the oracle (its OpenMP build: the same loop on
+    # all host threads, bit-identical to the serial one)
+    a, b = u0.copy(), np.zeros_like(u0)
+    want = oracle.heat2d_steps(a, b, r, steps, omp=True)
+    assert np.max(np.abs(got - want)) <= TOL * np.max(np.abs(want))
+    del a, b, want
     fin = np.array([np.sqrt(np.sum(got[i * 1024:(i + 1) * 1024, j * 1024:(j + 1) * 1024]
                                    .astype(np.longdouble) ** 2))
                     for i in range(8) for j in range(8)], dtype=np.float64)

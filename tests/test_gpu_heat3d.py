@@ -98,8 +98,8 @@ def test_heat3d_translation_and_reflection_exact(dev):
 
 @pytest.mark.parametrize("shape", [(40, 72, 96), (9, 70, 131), (8, 8, 8), (21, 33, 64)])
 def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
-    """Every form of the 3D kernel (plane registers copied, rotated, rotated
-    with paired FP32 instructions, two planes per level with the z range split
+    """Every form of the 3D kernel (three rotated plane registers per level on
+    paired FP32 instructions, two planes per level with the z range split
     over the CTAs, the same with a cp.async plane ring, and with packed narrow
     tiles) and every z split give the bits of one plain step per launch
     of the default form; odd nx takes the scalar-load path, small nz the
@@ -109,7 +109,7 @@ def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     want = oracle.heat3d(u0.astype(np.float64), float(R), 9)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1", "heat3d.zchunks")}
     try:
-        for variant in (0, 1, 2, 3, 4, 6):
+        for variant in (2, 3, 4, 6):
             hxc.tune_set("heat3d.variant", variant)
             hxc.tune_set("heat3d.variant1", variant)
             for nch in (0, 1, 3):
@@ -129,12 +129,12 @@ def test_heat3d_streaming_one_step_form(dev, shape):
     """The streaming one-step kernel (one-step form 5): z chunks with a ragged
     last chunk, rows not filling the last CTA, a partial last warp in x, tiny
     and degenerate shapes, and an odd nx (which takes another form) give the
-    bits of the copied-plane form, step after step."""
+    bits of the three-plane form, step after step."""
     u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=360 + shape[0], nz=shape[0],
                                                  ny=shape[1]), dtype=np.float32)
     old = hxc.tune_get("heat3d.variant1")
     try:
-        hxc.tune_set("heat3d.variant1", 0)
+        hxc.tune_set("heat3d.variant1", 2)
         ref, _ = run3d(dev, u0, 7, "plain", 1)
         hxc.tune_set("heat3d.variant1", 5)
         for mode in ("plain", "graph", "fused"):
@@ -208,7 +208,7 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
     """The two-plane forms (variants 3, 4 and 6) split the (region, plane) pairs
     evenly over whatever grid they are launched with: one CTA, a few CTAs whose shares
     span several regions, and more CTAs than pairs (empty shares) all give the
-    bits of the copied-plane form (variant 0); 1..4 steps per launch."""
+    bits of the three-plane form (variant 2); 1..4 steps per launch."""
     u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=340 + shape[0], nz=shape[0],
                                                  ny=shape[1]), dtype=np.float32)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1")}
@@ -216,7 +216,7 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
     try:
         for steps in (1, 2, 3, 4):
             want = None
-            for variant, grid in ((0, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000),
+            for variant, grid in ((2, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000),
                                   (4, None), (4, 1), (4, 7), (4, 100000), (6, None), (6, 1),
                                   (6, 7), (6, 100000)):
                 hxc.tune_set("heat3d.variant", variant)
