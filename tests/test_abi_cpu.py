@@ -256,7 +256,7 @@ def test_host_norms_on_the_worker_pool():
     got = hxc.host_norms(arrays)
     want = [float(np.sqrt(np.sum(a.astype(np.longdouble) ** 2))) for a in arrays]
     assert got[0] == 0.0 and got[1] == 5.0
-    assert np.max(np.abs(got[2:] - want[2:]) / np.array(want[2:])) <= 1e-15
+    assert np.max(np.abs(got[2:] - want[2:]) / np.array(want[2:])) <= 2e-15  # bound 1.4e-15
     L = hxc.lib()
     assert L.hxc_host_norms(None, None, 2, None) == hxc.HXC_E_INVALID
 
