@@ -858,6 +858,8 @@ def oracle_protocol(warmup, steps):
                       "(one call each, continuing the evolution), OpenMP build (row loop on %d "
                       "threads; C, -O2, no FMA)" % (warmup, steps, k, threads),
             "seconds_per_step": per, "time_steps_per_step": k,
+            "seconds_per_step_min_median_max": [min(times), statistics.median(times), max(times)],
+            "note": "the host is shared with other GPUs' jobs: its timings vary from run to run",
             "single_thread": {"value": NY * NX * ks / el_s, "cores": 1,
                               "sample": "full field from u0, %d time steps in one call" % ks},
             **info}
