@@ -117,6 +117,7 @@ hxc_status hxc_heat1d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
                           double r, int steps, hxc_mode mode, int steps_per_launch,
                           const hxc_future *deps, int ndeps, hxc_future *out,
                           hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_heat1d_run");
     Ref<Device> d = dev_from_handle(dh);
     Ref<Buffer> u = buf_from_handle(uh), t = buf_from_handle(th);
     if (!d || !u || !t) return HXC_E_INVALID;
@@ -614,6 +615,7 @@ extern "C" {
 hxc_status hxc_heat2d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, const hxc_heat2d_cfg *cfg,
                           const hxc_future *deps, int ndeps, hxc_future *out,
                           hxc_future *field_ready, hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_heat2d_run");
     Ref<Device> d = dev_from_handle(dh);
     Ref<Buffer> u = buf_from_handle(uh), tb = buf_from_handle(th);
     if (!d || !u || !tb) return HXC_E_INVALID;
@@ -1008,6 +1010,7 @@ extern "C" {
 hxc_status hxc_heat2d_run_host_async(hxc_device dh, const double *host_u0, double *host_uT,
                                      const hxc_heat2d_cfg *cfg, const hxc_future *deps, int ndeps,
                                      hxc_future *out, hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_heat2d_run_host_async");
     Ref<Device> d = dev_from_handle(dh);
     if (!d) return HXC_E_INVALID;
     if (!cfg || !host_u0 || !host_uT || !out || cfg->ny <= 0 || cfg->nx <= 0 ||
@@ -1120,6 +1123,7 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dh, const double *host_u0, doubl
 
 hxc_status hxc_heat2d_run_host(hxc_device dh, const double *host_u0, double *host_uT,
                                const hxc_heat2d_cfg *cfg, hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_heat2d_run_host");
     hxc_future f = nullptr;
     hxc_status st = hxc_heat2d_run_host_async(dh, host_u0, host_uT, cfg, nullptr, 0, &f, stats_out);
     if (st) return st;
@@ -1160,6 +1164,7 @@ hxc_status hxc_heat3d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
                           int64_t nx, float r, int steps, hxc_mode mode, int steps_per_launch,
                           const hxc_future *deps, int ndeps, hxc_future *out,
                           hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_heat3d_run");
     Ref<Device> d = dev_from_handle(dh);
     Ref<Buffer> u = buf_from_handle(uh), t = buf_from_handle(th);
     if (!d || !u || !t) return HXC_E_INVALID;

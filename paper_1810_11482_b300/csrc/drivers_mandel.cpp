@@ -105,6 +105,7 @@ hxc_status hxc_png_write(const uint8_t *rgb, int64_t width, int64_t height, int 
 hxc_status hxc_mandelbrot_png(hxc_device dh, const hxc_mandelbrot_args *args, uint8_t *host_rgb,
                               const char *path, int level, int async_write, int slot,
                               const hxc_future *deps, int ndeps, hxc_future *out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_mandelbrot_png");
     if (!args || !host_rgb || !path || !out || level < -1 || level > 9 || args->width < 1 ||
         args->height < 1) {
         set_error("hxc_mandelbrot_png: NULL or invalid argument");

@@ -38,6 +38,7 @@ extern "C" {
 hxc_status hxc_partition_run(hxc_device dh, const double *host_x, double *host_r, int64_t n,
                              int parts, hxc_buffer work, const hxc_future *deps, int ndeps,
                              hxc_future *out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_partition_run");
     if (!out) {
         set_error("hxc_partition_run: NULL output");
         return HXC_E_INVALID;
@@ -86,6 +87,7 @@ hxc_status hxc_partition_run(hxc_device dh, const double *host_x, double *host_r
 
 hxc_status hxc_partition_run_native(hxc_device dh, const double *host_x, double *host_r, int64_t n,
                                     int parts, hxc_buffer work) {
+    hxc::drv::NvtxRange nvtx_range("hxc_partition_run_native");
     hxc_status st = check_args(host_x, host_r, n, parts, work, "hxc_partition_run_native");
     if (st) return st;
     Ref<Device> d = dev_from_handle(dh);

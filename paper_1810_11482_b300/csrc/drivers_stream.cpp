@@ -63,6 +63,7 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
                                             int64_t tiles_x, double r, int steps, int sequential,
                                             const hxc_future *deps, int ndeps, hxc_future *out,
                                             hxc_run_stats *stats) {
+    hxc::drv::NvtxRange nvtx_range("hxc_heat2d_stream_run");
     Ref<Device> d = dev_from_handle(dh);
     if (!d) return HXC_E_INVALID;
     if (!out || !host_a || !host_b || host_a == host_b || ny < 1 || nx < 1 || tiles_y < 1 ||

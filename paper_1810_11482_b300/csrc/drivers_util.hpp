@@ -7,11 +7,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "runtime.hpp"
 #include "tune.hpp"
 
 namespace hxc {
 namespace drv {
+
+// An NVTX range around the host-side issue of a run entry point (a no-op
+// unless a profiler is attached): `ncu --nvtx --nvtx-include "<name>/"`
+// then captures only the kernels that entry point launches.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kCopySlot0 = 224;  // slots used for snapshot device->host copies
 constexpr int kCopySlots = 16;

@@ -44,6 +44,7 @@ hxc_status hxc_varcoef_batch_run(hxc_device dh, hxc_buffer uh, hxc_buffer kh, co
                                  const double *cs, int64_t nprob, int steps, hxc_mode mode,
                                  const hxc_future *deps, int ndeps, hxc_future *out,
                                  hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_varcoef_batch_run");
     Ref<Device> d = dev_from_handle(dh);
     if (!d) return HXC_E_INVALID;
     if (!sides || !cs || nprob <= 0 || nprob > (1 << 24) || steps < 0 ||
@@ -255,6 +256,7 @@ hxc_status hxc_varcoef_batch_run(hxc_device dh, hxc_buffer uh, hxc_buffer kh, co
 hxc_status hxc_sqerr_seed(hxc_device dh, hxc_buffer uh, hxc_buffer th, hxc_buffer lh,
                           hxc_buffer loss_h, int64_t n, int slot, const hxc_future *deps, int ndeps,
                           hxc_future *out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_sqerr_seed");
     if (!out) {
         set_error("hxc_sqerr_seed: NULL output");
         return HXC_E_INVALID;
@@ -293,6 +295,7 @@ hxc_status hxc_varcoef_forward_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
                                    int64_t nx, double c, int steps, hxc_buffer uTh,
                                    const hxc_future *deps, int ndeps, hxc_future *out,
                                    hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_varcoef_forward_run");
     Ref<Device> d = dev_from_handle(dh);
     if (!d || ny <= 0 || nx <= 0 || steps < 0) {
         set_error("hxc_varcoef_forward_run: invalid arguments");
@@ -409,6 +412,15 @@ hxc_status adjoint_impl(hxc_device dh, hxc_buffer u0h, hxc_buffer tapeh, hxc_buf
         if (gk->ptr == gu0->ptr || (uT && (uT->ptr == gk->ptr || uT->ptr == gu0->ptr))) {
             set_error("%s: outputs alias", fn);
             return HXC_E_INVALID;
+        }
+        if (tape) {
+            // the gradients must not land inside the tape the run still reads
+            const char *t0 = (const char *)tape->ptr, *t1 = t0 + nb * std::max(1, nseg);
+            for (const void *o : {(const void *)gk->ptr, (const void *)gu0->ptr, (const void *)lT->ptr})
+                if ((const char *)o + nb > t0 && (const char *)o < t1) {
+                    set_error("%s: the tape overlaps lamT, gk or gu0", fn);
+                    return HXC_E_INVALID;
+                }
         }
     }
     std::vector<FutRef> dv;
@@ -597,6 +609,7 @@ hxc_status hxc_varcoef_adjoint_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
                                    hxc_mode mode, hxc_buffer gkh, hxc_buffer gu0h, hxc_buffer uTh,
                                    const hxc_future *deps, int ndeps, hxc_future *out,
                                    hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_varcoef_adjoint_run");
     if (!u0h) {
         set_error("hxc_varcoef_adjoint_run: u0 is NULL");
         return HXC_E_INVALID;
@@ -610,6 +623,7 @@ hxc_status hxc_varcoef_adjoint_tape(hxc_device dh, hxc_buffer tapeh, hxc_buffer 
                                     hxc_mode mode, hxc_buffer gkh, hxc_buffer gu0h,
                                     const hxc_future *deps, int ndeps, hxc_future *out,
                                     hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_varcoef_adjoint_tape");
     if (!tapeh) {
         set_error("hxc_varcoef_adjoint_tape: tape is NULL");
         return HXC_E_INVALID;
@@ -632,6 +646,7 @@ hxc_status hxc_varcoef_forward_tape(hxc_device dh, hxc_buffer u0h, hxc_buffer kh
                                     int64_t nx, double c, int steps, int every, hxc_buffer uTh,
                                     hxc_buffer tapeh, const hxc_future *deps, int ndeps,
                                     hxc_future *out, hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_varcoef_forward_tape");
     Ref<Device> d = dev_from_handle(dh);
     if (!d || ny <= 0 || nx <= 0 || steps < 0 || every < 0) {
         set_error("hxc_varcoef_forward_tape: invalid arguments");

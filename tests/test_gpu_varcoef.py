@@ -201,6 +201,12 @@ def test_checkpoint_tape_matches_adjoint_run(dev):
     small = dev.buffer(u0.nbytes)
     with pytest.raises(hxc.HxcError):
         hxc.varcoef_forward_tape(dev, bu, bk, ny, nx, c, 10, dev.buffer(u0.nbytes), small, 3)
+    # outputs that would overwrite the tape while the run reads it are rejected
+    big = dev.buffer(4 * u0.nbytes)
+    hxc.varcoef_forward_tape(dev, bu, bk, ny, nx, c, 10, dev.buffer(u0.nbytes), big, 3)[0].get()
+    inside = dev.wrap(big.ptr + u0.nbytes, u0.nbytes)
+    with pytest.raises(hxc.HxcError):
+        hxc.varcoef_adjoint_tape(dev, big, bk, bl, ny, nx, c, 10, inside, dev.buffer(u0.nbytes), 3)
     with pytest.raises(hxc.HxcError):
         hxc.varcoef_adjoint_tape(dev, small, bk, bl, ny, nx, c, 10, dev.buffer(u0.nbytes),
                                  dev.buffer(u0.nbytes), 3)
