@@ -38,12 +38,15 @@ def _stale(path):
 def _declare_steps(L):
     L.ora_heat2d_steps.argtypes = [_dp, _dp, _i64, _i64, ctypes.c_double, ctypes.c_int]
     L.ora_heat2d_steps.restype = ctypes.c_void_p
+    L.ora_heat3d_steps.argtypes = [_dp, _dp, _i64, _i64, _i64, ctypes.c_double, ctypes.c_int]
+    L.ora_heat3d_steps.restype = ctypes.c_void_p
     L.ora_threads.restype = ctypes.c_int
 
 
 def lib_omp():
     """The OpenMP build (liboracle_omp.so): only the row loop of the 2D
-    stepping routine differs, and only in running on all threads."""
+    stepping routine and the plane loop of the 3D one differ, and only in
+    running on all threads."""
     global _lib_omp
     if _lib_omp is None:
         if _stale(_LIB_OMP):
@@ -200,6 +203,18 @@ def heat3d(u0, r, steps):
     nz, ny, nx = u0.shape
     lib().ora_heat3d(_p(u0), _p(out), nz, ny, nx, r, steps)
     return out
+
+
+def heat3d_steps(a, b, r, steps, omp=False):
+    """3D FTCS as heat3d, stepping the caller's C-contiguous float64 arrays of
+    shape (nz, ny, nx) in place (a holds u^0, b is scratch).  Returns whichever
+    of a, b holds u^steps.  omp=True runs the OpenMP build."""
+    assert a.dtype == np.float64 and b.dtype == np.float64 and a.shape == b.shape and a.ndim == 3
+    assert a.flags.c_contiguous and b.flags.c_contiguous
+    L = lib_omp() if omp else lib()
+    nz, ny, nx = a.shape
+    res = L.ora_heat3d_steps(_p(a), _p(b), nz, ny, nx, r, steps)
+    return a if res == a.ctypes.data else b
 
 
 def varcoef2d(u0, kappa, c, steps):

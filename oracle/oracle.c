@@ -166,14 +166,17 @@ void ora_tile_norms(const double *u, i64 ny, i64 nx, i64 ty, i64 tx, double *nor
 }
 
 /* 3D FTCS, 7-point Laplacian, periodic in all three directions, FP64.
- * Layout x fastest: index (k, i, j) = (z, y, x) -> (k*ny + i)*nx + j. */
-void ora_heat3d(const double *u0, double *out, i64 nz, i64 ny, i64 nx, double r, int steps) {
-    i64 n = nz * ny * nx;
-    double *a = (double *)malloc(sizeof(double) * n);
-    double *b = (double *)malloc(sizeof(double) * n);
-    memcpy(a, u0, sizeof(double) * n);
+ * Layout x fastest: index (k, i, j) = (z, y, x) -> (k*ny + i)*nx + j.
+ * Steps caller-owned ping-pong arrays like ora_heat2d_steps (a holds u^0;
+ * returns the array holding u^steps); the planes of a step are independent,
+ * so the OpenMP build runs the plane loop on all threads with the same
+ * operations on every cell. */
+double *ora_heat3d_steps(double *a, double *b, i64 nz, i64 ny, i64 nx, double r, int steps) {
 #define IDX3(k, i, j) ((wrap((k), nz) * ny + wrap((i), ny)) * nx + wrap((j), nx))
     for (int t = 0; t < steps; t++) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (i64 k = 0; k < nz; k++)
             for (i64 i = 0; i < ny; i++)
                 for (i64 j = 0; j < nx; j++) {
@@ -187,7 +190,16 @@ void ora_heat3d(const double *u0, double *out, i64 nz, i64 ny, i64 nx, double r,
         double *tmp = a; a = b; b = tmp;
     }
 #undef IDX3
-    memcpy(out, a, sizeof(double) * n);
+    return a;
+}
+
+void ora_heat3d(const double *u0, double *out, i64 nz, i64 ny, i64 nx, double r, int steps) {
+    i64 n = nz * ny * nx;
+    double *a = (double *)malloc(sizeof(double) * n);
+    double *b = (double *)malloc(sizeof(double) * n);
+    memcpy(a, u0, sizeof(double) * n);
+    double *res = ora_heat3d_steps(a, b, nz, ny, nx, r, steps);
+    memcpy(out, res, sizeof(double) * n);
     free(a); free(b);
 }
 

@@ -157,10 +157,11 @@ def test_heat3d_medium_vs_oracle_200_steps(dev):
 
 
 def test_heat3d_full_size_windows(dev):
-    """512^3, r = 0.15f, 200 steps in 50 launches of 4 steps: windows of the
-    result checked against the oracle run on a periodic window of 20 steps'
-    reach (a separate 20-step GPU run), plus the full 200-step result's
-    sum (conserved under periodic boundaries) and maximum principle."""
+    """512^3, r = 0.15f, 200 steps in 50 launches of 4 steps: the whole
+    200-step field against the oracle, windows of a 20-step run against the
+    oracle run on a periodic window of 20 steps' reach, plus the 200-step
+    result's sum (conserved under periodic boundaries) and maximum
+    principle."""
     n = 512
     u0 = synth.heat3d_input(n, seed=3)
     got20, _ = run3d(dev, u0, 20, "fused", 4)
@@ -174,6 +175,12 @@ def test_heat3d_full_size_windows(dev):
         assert relerr(mine, want, scale=1.0) <= TOL32
     got, st = run3d(dev, u0, 200, "fused", 4)
     assert st.kernel_launches == 50
+    # the whole field against the oracle (its OpenMP build) from the FP32 input
+    a = u0.astype(np.float64)
+    b = np.zeros_like(a)
+    want = oracle.heat3d_steps(a, b, float(R), 200, omp=True)
+    assert relerr(got, want) <= TOL32
+    del a, b, want
     s0 = math.fsum(u0.astype(np.float64).ravel())
     s1 = math.fsum(got.astype(np.float64).ravel())
     assert abs(s1 - s0) / s0 <= 1e-5

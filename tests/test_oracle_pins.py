@@ -197,6 +197,20 @@ def test_heat2d_stepping_builds_agree(ny, nx, steps):
     assert oracle.threads(False) == 1 and oracle.threads(True) >= 1
 
 
+@pytest.mark.parametrize("shape,steps", [((1, 1, 1), 3), ((7, 3, 130), 4), ((33, 21, 40), 5)])
+def test_heat3d_stepping_builds_agree(shape, steps):
+    """The caller-buffer 3D stepping routine equals heat3d, and its OpenMP
+    build (planes on all threads) equals the serial build bit for bit."""
+    nz, ny, nx = shape
+    u0 = synth.uniform(91 + nx, nz * ny * nx, lo=-1.0, hi=1.0).reshape(shape)
+    want = oracle.heat3d(u0, 0.15, steps)
+    for omp in (False, True):
+        a, b = u0.copy(), np.full_like(u0, np.nan)
+        got = oracle.heat3d_steps(a, b, 0.15, steps, omp=omp)
+        assert got is (a if steps % 2 == 0 else b)
+        assert np.array_equal(got, want), omp
+
+
 def test_heat2d_max_principle():
     u0 = synth.bumps2d(40, 40, seed=34, nbumps=3, sigma=0.1)
     ut = oracle.heat2d(u0, 0.25, 100)
