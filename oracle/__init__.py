@@ -35,6 +35,11 @@ def _stale(path):
     return not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(src)
 
 
+def _declare_batch(L):
+    L.ora_varcoef2d_batch.argtypes = [_dp, _dp, _dp, ctypes.POINTER(_i64),
+                                      ctypes.POINTER(_i64), _dp, _i64, ctypes.c_int]
+
+
 def _declare_steps(L):
     L.ora_heat2d_steps.argtypes = [_dp, _dp, _i64, _i64, ctypes.c_double, ctypes.c_int]
     L.ora_heat2d_steps.restype = ctypes.c_void_p
@@ -45,14 +50,15 @@ def _declare_steps(L):
 
 def lib_omp():
     """The OpenMP build (liboracle_omp.so): only the row loop of the 2D
-    stepping routine and the plane loop of the 3D one differ, and only in
-    running on all threads."""
+    stepping routine, the plane loop of the 3D one and the problem loop of
+    the batch differ, and only in running on all threads."""
     global _lib_omp
     if _lib_omp is None:
         if _stale(_LIB_OMP):
             build()
         L = ctypes.CDLL(_LIB_OMP)
         _declare_steps(L)
+        _declare_batch(L)
         _lib_omp = L
     return _lib_omp
 
@@ -78,8 +84,7 @@ def lib():
         L.ora_varcoef2d_adjoint.argtypes = [_dp, _dp, _dp, _i64, _i64, ctypes.c_double,
                                             ctypes.c_int, _dp, _dp]
         L.ora_varcoef2d_adjoint.restype = ctypes.c_double
-        L.ora_varcoef2d_batch.argtypes = [_dp, _dp, _dp, ctypes.POINTER(_i64),
-                                          ctypes.POINTER(_i64), _dp, _i64, ctypes.c_int]
+        _declare_batch(L)
         _fp = ctypes.POINTER(ctypes.c_float)
         L.ora_mandelbrot_counts.argtypes = [_fp, _fp, ctypes.POINTER(ctypes.c_int32), _i64,
                                             ctypes.c_int32]
@@ -249,8 +254,9 @@ def varcoef2d_adjoint(u0, kappa, utgt, c, steps):
     return loss, gk, gu
 
 
-def varcoef2d_batch(u0, kappa, sides, offsets, cs, steps):
-    """Independent square problems packed back to back; each stepped with its own c."""
+def varcoef2d_batch(u0, kappa, sides, offsets, cs, steps, omp=False):
+    """Independent square problems packed back to back; each stepped with its own c.
+    omp=True runs the OpenMP build (problems spread over the host threads)."""
     u0 = _f64(u0)
     kappa = _f64(kappa)
     out = np.empty_like(u0)
@@ -258,6 +264,7 @@ def varcoef2d_batch(u0, kappa, sides, offsets, cs, steps):
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     cs = _f64(cs)
     P = ctypes.POINTER(_i64)
-    lib().ora_varcoef2d_batch(_p(u0), _p(kappa), _p(out), sides.ctypes.data_as(P),
-                              offsets.ctypes.data_as(P), _p(cs), sides.size, steps)
+    L = lib_omp() if omp else lib()
+    L.ora_varcoef2d_batch(_p(u0), _p(kappa), _p(out), sides.ctypes.data_as(P),
+                          offsets.ctypes.data_as(P), _p(cs), sides.size, steps)
     return out

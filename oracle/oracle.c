@@ -329,10 +329,15 @@ void ora_varcoef2d_transpose_step(const double *lam, double *out, const double *
 
 /* A batch of independent variable-diffusivity problems (square sides
  * side[p], packed one after another, problem p starting at offset[p]),
- * each stepped `steps` times with its own c[p].  The oracle simply loops. */
+ * each stepped `steps` times with its own c[p].  The oracle simply loops;
+ * the problems share nothing, so the OpenMP build hands them to its threads
+ * (each problem computed by one thread, exactly as in the serial loop). */
 void ora_varcoef2d_batch(const double *u0, const double *kap, double *out,
                          const i64 *side, const i64 *offset, const double *c,
                          i64 nprob, int steps) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
     for (i64 p = 0; p < nprob; p++)
         ora_varcoef2d(u0 + offset[p], kap + offset[p], out + offset[p],
                       side[p], side[p], c[p], steps);

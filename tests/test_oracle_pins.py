@@ -211,6 +211,14 @@ def test_heat3d_stepping_builds_agree(shape, steps):
         assert np.array_equal(got, want), omp
 
 
+def test_batch_builds_agree():
+    """The OpenMP build of the batch (problems on all threads) equals the
+    serial build bit for bit, on ragged problem sizes."""
+    sides, offs, kap, u0, cs = synth.batch_input(nprob=23, seed=413, smin=1, smax=40)
+    want = oracle.varcoef2d_batch(u0, kap, sides, offs, cs, 6)
+    assert np.array_equal(oracle.varcoef2d_batch(u0, kap, sides, offs, cs, 6, omp=True), want)
+
+
 def test_heat2d_max_principle():
     u0 = synth.bumps2d(40, 40, seed=34, nbumps=3, sigma=0.1)
     ut = oracle.heat2d(u0, 0.25, 100)
