@@ -202,6 +202,14 @@ hxc_status hxc_promise_set(hxc_future promise, hxc_status status);
  * wide and one-shot; after_ops < 0 disarms.  Returns HXC_E_INVALID for
  * status == HXC_OK with after_ops >= 0. */
 hxc_status hxc_debug_inject(int64_t after_ops, hxc_status status);
+/* The paper has no counterpart to this call.  Device-side waits of the
+ * library's kernels are bounded (the 3D form 7 waits on shared-memory
+ * barriers for its TMA copies); a wait that runs out sets a bit in a
+ * device-wide record and its CTA leaves without finishing its work.  This
+ * call synchronises the device's slots, then reads and clears the record:
+ * *flags = 0 when no wait ran out since the last call, bit 0 set when a 3D
+ * TMA wait did. */
+hxc_status hxc_debug_wait_errors(hxc_device dev, uint32_t *flags);
 /* Interop with foreign CUDA streams (e.g. torch's current stream):
  * a future for everything issued so far on `stream` ... */
 hxc_status hxc_future_from_stream(hxc_device dev, void *stream, hxc_future *out);
@@ -630,9 +638,14 @@ hxc_status hxc_varcoef_adjoint_tape(hxc_device dev, hxc_buffer tape, hxc_buffer 
  *                  6 = form 4 with packed narrow tiles (the columns and rows
  *                  left over by the 64 - 2T wide output tiles go to 16-wide
  *                  regions run four or sixteen to a CTA in lane segments and
- *                  warp groups; the default).  Forms 3, 4 and 6 launched with
- *                  an hxc_launch_cfg take 512 threads per CTA and any grid
- *                  (form 6 at least 2 CTAs when it has both kinds of tiles).
+ *                  warp groups; the default), 7 = form 6 with the input
+ *                  planes of the regions that lie inside the field (no
+ *                  periodic wrap; 4 steps per launch, nx % 4 == 0) copied by
+ *                  TMA tensor copies completing on shared-memory barriers
+ *                  (bounded waits, see hxc_debug_wait_errors).  Forms 3, 4, 6
+ *                  and 7 launched with an hxc_launch_cfg take 512 threads per
+ *                  CTA and any grid (forms 6 and 7 at least one CTA per kind
+ *                  of tile they have).
  *   "heat3d.variant1"  the form used for one-step launches (PLAIN mode and
  *                  single-step remainders), the values above plus 5 = a
  *                  streaming kernel (4 adjacent x cells per thread, 16-byte

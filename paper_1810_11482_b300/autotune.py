@@ -102,15 +102,15 @@ def tune(quick=False, log=print):
     log("heat3d")
     run3 = lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 8, "fused", 4, d)[0]
     hxc.tune_set("heat3d.zchunks", 0)
-    best3 = _search(timer, {"heat3d.variant": [2, 3, 4, 6]}, run3, log)
-    # the z split applies to the form that cuts z into chunks (2); forms 3, 4
-    # and 6 split the (region, plane) pairs evenly over the SMs themselves
+    best3 = _search(timer, {"heat3d.variant": [2, 3, 4, 6, 7]}, run3, log)
+    # the z split applies to the form that cuts z into chunks (2); forms 3, 4,
+    # 6 and 7 split the (region, plane) pairs evenly over the SMs themselves
     if best3["heat3d.variant"] <= 2:
         best3.update(_search(timer, {"heat3d.zchunks": [0, 1, 2, 3, 4, 6, 8]}, run3, log))
     result.update(best3)
     # one-step launches (PLAIN mode) choose their form separately
     run31 = lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 8, "plain", 1, d)[0]
-    result.update(_search(timer, {"heat3d.variant1": [2, 3, 4, 5, 6]}, run31, log))
+    result.update(_search(timer, {"heat3d.variant1": [2, 3, 4, 5, 6, 7]}, run31, log))
     # steps per fused launch when the caller passes 0 (12 steps: whole
     # launches for 2, 3 and 4)
     run3t = lambda d: hxc.heat3d_run(dev, a, b, (n3, n3, n3), 0.15, 12, "fused", 0, d)[0]

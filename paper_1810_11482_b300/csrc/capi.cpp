@@ -523,6 +523,20 @@ hxc_status hxc_debug_inject(int64_t after_ops, hxc_status status) {
     return HXC_OK;
 }
 
+hxc_status hxc_debug_wait_errors(hxc_device dh, uint32_t *flags) {
+    CHECK_OUT(flags);
+    Ref<Device> d = dev_from_handle(dh);
+    if (!d) return HXC_E_INVALID;
+    hxc_status st = d->make_current();
+    if (st) return st;
+    if ((st = hxc_device_synchronize(dh))) return st;
+    unsigned v = 0;
+    cudaError_t e = k::heat3d_wait_errors(&v);
+    if (e != cudaSuccess) return cuda_status(e, "hxc_debug_wait_errors");
+    *flags = v;
+    return HXC_OK;
+}
+
 hxc_status hxc_future_from_stream(hxc_device dh, void *stream, hxc_future *out) {
     CHECK_OUT(out);
     Ref<Device> d = dev_from_handle(dh);

@@ -19,6 +19,11 @@
 // cp.async ring of input planes), 6 (form 4 with packed narrow tiles), and
 // for one-step launches 5 (a streaming kernel).
 #include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include <cuda.h>  // CUtensorMap: the TMA descriptor passed to form 7
+#include <cudaTypedefs.h>
 
 #include "f32x2.cuh"
 #include "kernels.cuh"
@@ -414,10 +419,98 @@ __device__ __forceinline__ void v4_fetch(f2 *__restrict__ ring, int slot, const 
     cp_commit();
 }
 
-template <int T, int Q, int SW>
+// How the level-0 planes reach the ring: each thread copies its own cells
+// with cp.async (any region), waiting for its own copies.
+struct CpFetch {
+    f2 *ring;
+    const float *src;
+    size_t plane;
+    const unsigned *row;
+    unsigned gx0, gx1;
+    bool pair;
+    int lane, warp;
+    __device__ __forceinline__ void issue(int slot, int z) {
+        const unsigned r4[4] = {row[0], row[1], row[2], row[3]};
+        v4_fetch(ring, slot, src + (size_t)z * plane, r4, gx0, gx1, pair, lane, warp);
+    }
+    __device__ __forceinline__ void wait(int) { cp_wait<V4_D>(); }
+    __device__ __forceinline__ void drain() { cp_wait<0>(); }
+    __device__ __forceinline__ void sync() { __syncthreads(); }
+    static constexpr bool failed = false;
+};
+
+// Form 7: one thread copies a region's whole 64 x 64 input plane into the
+// ring slot with a TMA tensor copy (cp.async.bulk.tensor, completion on the
+// slot's mbarrier); every thread waits on the barrier's phase before reading
+// the slot.  Only regions that lie inside the field are fetched this way (a
+// TMA tile does not wrap around the periodic edges).  Waits are bounded: a
+// wait that runs out records it in g_heat3d_wait_errors, the CTA agrees on
+// the failure at its next barrier, stops issuing copies, waits (again
+// bounded) for the copies still in flight and leaves.
+__device__ unsigned g_heat3d_wait_errors;
+
+constexpr unsigned kTmaTileBytes = 64 * 64 * sizeof(float);
+constexpr int kTmaMaxTries = 1 << 22;
+
+struct TmaFetch {
+    f2 *ring;
+    const CUtensorMap *map;
+    unsigned bars;      // shared-space address of V4_RS mbarriers, 8 bytes each
+    int x0, y0;         // the region's origin (inside the field)
+    unsigned phase;     // per slot: parity of the barrier phase to wait for next
+    unsigned inflight;  // per slot: a copy issued and not yet waited for
+    int failed;
+    __device__ __forceinline__ void issue(int slot, int z) {
+        if (failed) return;
+        if (threadIdx.x == 0) {
+            const unsigned bar = bars + 8u * (unsigned)slot;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(ring + (size_t)slot * V3_H * 32);
+            // the slot's previous contents were read through the generic
+            // proxy (ordered by the last CTA barrier); order those reads
+            // before the async-proxy write
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(bar), "r"(kTmaTileBytes) : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];"
+                :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x0), "r"(y0), "r"(z),
+                   "r"(bar)
+                : "memory");
+        }
+        inflight |= 1u << slot;
+    }
+    __device__ __forceinline__ bool wait_slot(int slot) {
+        const unsigned bar = bars + 8u * (unsigned)slot, par = (phase >> slot) & 1u;
+        unsigned done = 0;
+        for (int it = 0; it < kTmaMaxTries && !done; ++it)
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+                " selp.u32 %0, 1, 0, p; }"
+                : "=r"(done) : "r"(bar), "r"(par) : "memory");
+        if (!done) {
+            atomicOr(&g_heat3d_wait_errors, 1u);
+            return false;
+        }
+        phase ^= 1u << slot;
+        inflight &= ~(1u << slot);
+        return true;
+    }
+    __device__ __forceinline__ void wait(int slot) {
+        if (!failed && !wait_slot(slot)) failed = 1;
+    }
+    __device__ __forceinline__ void drain() {
+        for (int sl = 0; sl < V4_RS; sl++)
+            if (inflight & (1u << sl)) wait_slot(sl);
+    }
+    // the per-iteration CTA barrier, which also makes a failure CTA-uniform
+    __device__ __forceinline__ void sync() { failed = __syncthreads_or(failed); }
+};
+
+template <int T, int Q, int SW, class F>
 __device__ __forceinline__ void v4_iter(f2 (&X)[T][4], f2 (&Y)[T][4], f2 (&Pp)[T][4],
                                         f2 *__restrict__ ring, int slot, int fslot,
-                                        f2 *__restrict__ Sb, const float *__restrict__ src,
+                                        f2 *__restrict__ Sb, F &fetch,
                                         float *__restrict__ dst, const unsigned (&row)[4],
                                         unsigned gx0, unsigned gx1, bool pair, int &zf, int nz,
                                         size_t plane, bool store, int zout, unsigned omask,
@@ -425,10 +518,10 @@ __device__ __forceinline__ void v4_iter(f2 (&X)[T][4], f2 (&Y)[T][4], f2 (&Pp)[T
                                         f2 m6) {
     f2(&C)[T][4] = Q ? Y : X;
     f2(&N)[T][4] = Q ? X : Y;
-    // fetch plane V4_D ahead, then wait for this iteration's plane (own copies)
+    // fetch plane V4_D ahead, then wait for this iteration's plane
     zf = zf + 1 < nz ? zf + 1 : 0;
-    v4_fetch(ring, fslot, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
-    cp_wait<V4_D>();
+    fetch.issue(fslot, zf);
+    fetch.wait(slot);
     const f2 *rs = ring + (size_t)slot * V3_H * 32;
 #pragma unroll
     for (int k = 0; k < 4; k++) N[0][k] = rs[(4 * warp + k) * 32 + lane];
@@ -455,7 +548,7 @@ __device__ __forceinline__ void v4_iter(f2 (&X)[T][4], f2 (&Y)[T][4], f2 (&Pp)[T
         Sb[(((t - 1) * V3_NW + warp) * 2 + 0) * 32 + lane] = N[t][0];
         Sb[(((t - 1) * V3_NW + warp) * 2 + 1) * 32 + lane] = N[t][3];
     }
-    __syncthreads();
+    fetch.sync();
 #pragma unroll
     for (int t = 0; t < T; t++) {
         const f2 up = t == 0 ? rs[ru * 32 + lane] : Sb[(((t - 1) * V3_NW + wu) * 2 + 1) * 32 + lane];
@@ -486,7 +579,7 @@ __global__ void __launch_bounds__(V3_NW * 32, 1)
     k_heat3d_v4(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
                 float r) {
     constexpr int BX = 64 - 2 * T, BY = V3_H - 2 * T;
-    extern __shared__ __align__(16) f2 v4_smem[];
+    extern __shared__ __align__(128) f2 v4_smem[];
     f2 *ring = v4_smem;
     f2 *sbase = v4_smem + (size_t)V4_RS * V3_H * 32;
     constexpr int SB = (T > 1 ? T - 1 : 1) * V3_NW * 2 * 32;
@@ -530,31 +623,32 @@ __global__ void __launch_bounds__(V3_NW * 32, 1)
         // iteration j receives level-0 plane za - T + j (ring slot j % V4_RS)
         // and emits level-T plane za - 2T + j (stored for j >= 2T)
         const int iters = (zb - za) + 2 * T;
+        CpFetch fetch{ring, src, plane, row, gx0, gx1, pair, lane, warp};
         int zf = wrapi(za - T, nz);
-        v4_fetch(ring, 0, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+        fetch.issue(0, zf);
 #pragma unroll
         for (int q = 1; q < V4_D; q++) {
             zf = zf + 1 < nz ? zf + 1 : 0;
-            v4_fetch(ring, q, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+            fetch.issue(q, zf);
         }
         int slot = 0;
         for (int j = 0; j < iters; j += 2) {
             int fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
-            v4_iter<T, 0, 32>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
+            v4_iter<T, 0, 32>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, fetch, dst, row, gx0, gx1, pair,
                           zf, nz, plane, j >= 2 * T, za - 2 * T + j, omask, lane, warp, ru, rd, wu,
                           wd, r2, m6);
             buf ^= 1;
             slot = slot + 1 < V4_RS ? slot + 1 : 0;
             if (j + 1 >= iters) break;
             fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
-            v4_iter<T, 1, 32>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1, pair,
+            v4_iter<T, 1, 32>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, fetch, dst, row, gx0, gx1, pair,
                           zf, nz, plane, j + 1 >= 2 * T, za - 2 * T + j + 1, omask, lane, warp, ru,
                           rd, wu, wd, r2, m6);
             buf ^= 1;
             slot = slot + 1 < V4_RS ? slot + 1 : 0;
         }
         // the copies fetched past the segment land before the ring is reused
-        cp_wait<0>();
+        fetch.drain();
         __syncthreads();
     }
 }
@@ -595,6 +689,11 @@ struct Tiling3 {
     int fx4, fy4, nxn4, nyn4;   // the same in blocks of four (rounded up)
     int ff, fn, nf, nn;         // units of each kind per plane
     int ctas_wide;
+    // form 7: full x full tiles whose regions lie inside the field (no
+    // periodic wrap), x tiles [ia, ia + nix) by y tiles [ja, ja + niy),
+    // fetched by TMA in CTAs [0, ctas_tma); the other ne = ff - nix*niy full
+    // tiles and the full-x narrow-y units in CTAs [ctas_tma, ctas_wide)
+    int ia, nix, ja, niy, ne, ctas_tma;
 };
 
 inline Tiling3 tiling3(int ny, int nx, int T) {
@@ -613,7 +712,21 @@ inline Tiling3 tiling3(int ny, int nx, int T) {
     t.nf = t.nxn * t.fy4;
     t.nn = t.nxn4 * t.nyn4;
     t.ctas_wide = 0;
+    t.ia = t.nix = t.ja = t.niy = 0;
+    t.ne = t.ff;
+    t.ctas_tma = 0;
     return t;
+}
+
+// Interior tiles of an axis of n cells: those whose 64-cell region starts
+// at or after 0 and ends at or before n.
+inline void interior3(int n, int full, int T, int *lo, int *cnt) {
+    const int fw = 64 - 2 * T;
+    const int a = (T + fw - 1) / fw;                 // first i with i*fw - T >= 0
+    const int b = n + T - 64 >= 0 ? (n + T - 64) / fw : -1;  // last i ending inside
+    const int hi = std::min(b, full - 1);
+    *lo = a;
+    *cnt = hi >= a ? hi - a + 1 : 0;
 }
 
 // Region of unit u for this thread: output origin (ox, oy), stored extent
@@ -665,30 +778,121 @@ __device__ __forceinline__ int4 v6_decode(int u, int ny, int nx, const Tiling3 &
     return make_int4(ox, oy, wx | (hy << 8), gw | ((valid ? 1 : 0) << 8));
 }
 
-// The (unit, plane) pairs [w0, w1) of one group: SW = 32 for the wide
-// units, 8 for the narrow ones.
-template <int T, int SW>
-__device__ __forceinline__ void v6_units_run(const float *__restrict__ src, float *__restrict__ dst,
-                                             int nz, int ny, int nx, float r, const Tiling3 &tl,
-                                             int64_t w0, int64_t w1) {
-    extern __shared__ __align__(16) f2 v4_smem[];
+// All iterations of one unit over planes [za, zb) with the ring filled by
+// `fetch`.  Returns false when the fetch failed (form 7's bounded waits).
+template <int T, int SW, class F>
+__device__ __forceinline__ bool unit_loop(F &fetch, f2 *__restrict__ ring, f2 *__restrict__ sbase,
+                                          int &buf, float *__restrict__ dst,
+                                          const unsigned (&row)[4], unsigned gx0, unsigned gx1,
+                                          bool pair, int nz, size_t plane, int za, int zb,
+                                          unsigned omask, int lane, int warp, int ru, int rd,
+                                          int wu, int wd, f2 r2, f2 m6) {
+    constexpr int SB = (T > 1 ? T - 1 : 1) * V3_NW * 2 * 32;
+    f2 X[T][4], Y[T][4], Pp[T][4];
+#pragma unroll
+    for (int t = 0; t < T; t++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) X[t][k] = Y[t][k] = Pp[t][k] = 0ull;
+    // iteration j receives level-0 plane za - T + j (ring slot j % V4_RS)
+    // and emits level-T plane za - 2T + j (stored for j >= 2T)
+    const int iters = (zb - za) + 2 * T;
+    int zf = wrapi(za - T, nz);
+    fetch.issue(0, zf);
+#pragma unroll
+    for (int q = 1; q < V4_D; q++) {
+        zf = zf + 1 < nz ? zf + 1 : 0;
+        fetch.issue(q, zf);
+    }
+    int slot = 0;
+    for (int j = 0; j < iters; j += 2) {
+        int fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
+        v4_iter<T, 0, SW>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, fetch, dst, row, gx0, gx1,
+                          pair, zf, nz, plane, j >= 2 * T, za - 2 * T + j, omask, lane, warp, ru,
+                          rd, wu, wd, r2, m6);
+        buf ^= 1;
+        slot = slot + 1 < V4_RS ? slot + 1 : 0;
+        if (j + 1 >= iters || fetch.failed) break;
+        fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
+        v4_iter<T, 1, SW>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, fetch, dst, row, gx0, gx1,
+                          pair, zf, nz, plane, j + 1 >= 2 * T, za - 2 * T + j + 1, omask, lane,
+                          warp, ru, rd, wu, wd, r2, m6);
+        buf ^= 1;
+        slot = slot + 1 < V4_RS ? slot + 1 : 0;
+        if (fetch.failed) break;
+    }
+    // the copies fetched past the segment land before the ring is reused
+    fetch.drain();
+    __syncthreads();
+    return !fetch.failed;
+}
+
+// Form 7's decodes.  G = 2: interior full x full tiles (i, j) in
+// [ia, ia + nix) x [ja, ja + niy).  G = 3: the other full x full tiles (the
+// rows of tiles outside [ja, ja + niy), then the columns outside
+// [ia, ia + nix) of the rows inside), then the full-x narrow-y units.
+template <int T, int G>
+__device__ __forceinline__ int4 v7_decode(int u, int ny, int nx, const Tiling3 &tl, int lane,
+                                          int warp) {
+    constexpr int FW = 64 - 2 * T;
+    if (G == 2) {
+        const int ox = (tl.ia + u % tl.nix) * FW, oy = (tl.ja + u / tl.nix) * FW;
+        return make_int4(ox, oy, min(FW, nx - ox) | (min(FW, ny - oy) << 8), V3_NW | (1 << 8));
+    }
+    if (u >= tl.ne) return v6_decode<T, 32>(u - tl.ne + tl.ff, ny, nx, tl, lane, warp);
+    int i, j;
+    const int rows_out = (tl.fy - tl.niy) * tl.fx;
+    if (u < rows_out) {
+        const int jj = u / tl.fx;
+        j = jj < tl.ja ? jj : jj + tl.niy;
+        i = u % tl.fx;
+    } else {
+        const int k = u - rows_out, ncol = tl.fx - tl.nix;
+        j = tl.ja + k / ncol;
+        const int ii = k % ncol;
+        i = ii < tl.ia ? ii : ii + tl.nix;
+    }
+    const int ox = i * FW, oy = j * FW;
+    return make_int4(ox, oy, min(FW, nx - ox) | (min(FW, ny - oy) << 8), V3_NW | (1 << 8));
+}
+
+// The (unit, plane) pairs [w0, w1) of one group of CTAs.  G = 0: form 6's
+// wide units, 1: the narrow-x units (both forms), 2: form 7's interior
+// tiles (TMA), 3: form 7's other wide units.  SW = lanes per region in x.
+template <int T, int SW, int G>
+__device__ __forceinline__ void units_run(const float *__restrict__ src, float *__restrict__ dst,
+                                          int nz, int ny, int nx, float r, const Tiling3 &tl,
+                                          int64_t w0, int64_t w1, const CUtensorMap *map) {
+    extern __shared__ __align__(128) f2 v4_smem[];
+    __shared__ __align__(8) unsigned long long tma_bar[V4_RS];
     f2 *ring = v4_smem;
     f2 *sbase = v4_smem + (size_t)V4_RS * V3_H * 32;
-    constexpr int SB = (T > 1 ? T - 1 : 1) * V3_NW * 2 * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t plane = (size_t)ny * nx;
     const f2 r2 = pk(r, r), m6 = pk(-6.0f, -6.0f);
     int buf = 0;
+    unsigned tma_bars = 0, tma_phase = 0;
+    if constexpr (G == 2) {
+        tma_bars = (unsigned)__cvta_generic_to_shared(tma_bar);
+        if (threadIdx.x == 0) {
+            for (int sl = 0; sl < V4_RS; sl++)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tma_bars + 8u * sl)
+                             : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
 
     for (int64_t w = w0; w < w1;) {
         int64_t u = w / nz;
         const int za = (int)(w - u * nz);
         const int zb = (int)min((int64_t)nz, za + (w1 - w));
         w += zb - za;
-        // this thread's region of the unit (decoded out of line: inlined,
-        // the decode's temporaries push the level chain past the register
-        // budget)
-        const int4 geo = v6_decode<T, SW>((int)u, ny, nx, tl, lane, warp);
+        // this thread's region of the unit
+        int4 geo;
+        if constexpr (G == 0 || G == 1)
+            geo = v6_decode<T, SW>((int)u, ny, nx, tl, lane, warp);
+        else
+            geo = v7_decode<T, G>((int)u, ny, nx, tl, lane, warp);
         const int ox = geo.x, oy = geo.y, wx = geo.z & 0xff, hy = geo.z >> 8, gw = geo.w & 0xff;
         const bool valid = (geo.w >> 8) != 0;
         const int x0 = ox - T, y0 = oy - T;
@@ -710,40 +914,18 @@ __device__ __forceinline__ void v6_units_run(const float *__restrict__ src, floa
             omask |= (oy_ && ox1 ? 2u : 0u) << (2 * k);
         }
 
-        f2 X[T][4], Y[T][4], Pp[T][4];
-#pragma unroll
-        for (int t = 0; t < T; t++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) X[t][k] = Y[t][k] = Pp[t][k] = 0ull;
-        // iteration j receives level-0 plane za - T + j (ring slot j % V4_RS)
-        // and emits level-T plane za - 2T + j (stored for j >= 2T)
-        const int iters = (zb - za) + 2 * T;
-        int zf = wrapi(za - T, nz);
-        v4_fetch(ring, 0, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
-#pragma unroll
-        for (int q = 1; q < V4_D; q++) {
-            zf = zf + 1 < nz ? zf + 1 : 0;
-            v4_fetch(ring, q, src + (size_t)zf * plane, row, gx0, gx1, pair, lane, warp);
+        if constexpr (G == 2) {
+            TmaFetch fetch{ring, map, tma_bars, x0, y0, tma_phase, 0u, 0};
+            const bool ok = unit_loop<T, SW>(fetch, ring, sbase, buf, dst, row, gx0, gx1, pair, nz,
+                                             plane, za, zb, omask, lane, warp, ru, rd, wu, wd, r2,
+                                             m6);
+            tma_phase = fetch.phase;
+            if (!ok) return;  // a bounded wait ran out (recorded): leave
+        } else {
+            CpFetch fetch{ring, src, plane, row, gx0, gx1, pair, lane, warp};
+            unit_loop<T, SW>(fetch, ring, sbase, buf, dst, row, gx0, gx1, pair, nz, plane, za, zb,
+                             omask, lane, warp, ru, rd, wu, wd, r2, m6);
         }
-        int slot = 0;
-        for (int j = 0; j < iters; j += 2) {
-            int fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
-            v4_iter<T, 0, SW>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1,
-                              pair, zf, nz, plane, j >= 2 * T, za - 2 * T + j, omask, lane, warp,
-                              ru, rd, wu, wd, r2, m6);
-            buf ^= 1;
-            slot = slot + 1 < V4_RS ? slot + 1 : 0;
-            if (j + 1 >= iters) break;
-            fs = slot + V4_D < V4_RS ? slot + V4_D : slot + V4_D - V4_RS;
-            v4_iter<T, 1, SW>(X, Y, Pp, ring, slot, fs, sbase + buf * SB, src, dst, row, gx0, gx1,
-                              pair, zf, nz, plane, j + 1 >= 2 * T, za - 2 * T + j + 1, omask, lane,
-                              warp, ru, rd, wu, wd, r2, m6);
-            buf ^= 1;
-            slot = slot + 1 < V4_RS ? slot + 1 : 0;
-        }
-        // the copies fetched past the segment land before the ring is reused
-        cp_wait<0>();
-        __syncthreads();
     }
 }
 
@@ -756,11 +938,36 @@ __global__ void __launch_bounds__(V3_NW * 32, 1)
     const int64_t b = blockIdx.x;
     if (b < tl.ctas_wide) {
         const int64_t g = tl.ctas_wide;
-        v6_units_run<T, 32>(src, dst, nz, ny, nx, r, tl, work_wide * b / g, work_wide * (b + 1) / g);
+        units_run<T, 32, 0>(src, dst, nz, ny, nx, r, tl, work_wide * b / g,
+                            work_wide * (b + 1) / g, nullptr);
     } else {
         const int64_t g = gridDim.x - tl.ctas_wide, c = b - tl.ctas_wide;
-        v6_units_run<T, 8>(src, dst, nz, ny, nx, r, tl, work_narrow * c / g,
-                           work_narrow * (c + 1) / g);
+        units_run<T, 8, 1>(src, dst, nz, ny, nx, r, tl, work_narrow * c / g,
+                           work_narrow * (c + 1) / g, nullptr);
+    }
+}
+
+// Form 7: form 6 with the interior full tiles' planes fetched by TMA
+// (CTAs [0, ctas_tma)), the other wide units in [ctas_tma, ctas_wide) and the
+// narrow-x units in the rest, each group splitting its (unit, plane) pairs
+// evenly over its CTAs.
+template <int T>
+__global__ void __launch_bounds__(V3_NW * 32, 1)
+    k_heat3d_v7(const float *__restrict__ src, float *__restrict__ dst, int nz, int ny, int nx,
+                float r, const Tiling3 tl, const __grid_constant__ CUtensorMap map) {
+    const int64_t wt = (int64_t)tl.nix * tl.niy * nz;
+    const int64_t we = (int64_t)(tl.ne + tl.fn) * nz;
+    const int64_t wn = (int64_t)(tl.nf + tl.nn) * nz;
+    const int64_t b = blockIdx.x;
+    if (b < tl.ctas_tma) {
+        const int64_t g = tl.ctas_tma;
+        units_run<T, 32, 2>(src, dst, nz, ny, nx, r, tl, wt * b / g, wt * (b + 1) / g, &map);
+    } else if (b < tl.ctas_wide) {
+        const int64_t g = tl.ctas_wide - tl.ctas_tma, c = b - tl.ctas_tma;
+        units_run<T, 32, 3>(src, dst, nz, ny, nx, r, tl, we * c / g, we * (c + 1) / g, nullptr);
+    } else {
+        const int64_t g = gridDim.x - tl.ctas_wide, c = b - tl.ctas_wide;
+        units_run<T, 8, 1>(src, dst, nz, ny, nx, r, tl, wn * c / g, wn * (c + 1) / g, nullptr);
     }
 }
 
@@ -785,6 +992,86 @@ cudaError_t v6_launch(unsigned g, const float *src, float *dst, int nz, int ny, 
         tl.ctas_wide = (int)std::max<int64_t>(1, std::min<int64_t>(g - 1, cw));
     }
     k_heat3d_v6<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r, tl);
+    return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to
+// the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Splits g CTAs over groups with the given work in proportion (a group with
+// work gets at least one CTA; g is raised to the number of such groups).
+void split_ctas(unsigned &g, const int64_t (&work)[3], int (&ctas)[3]) {
+    int need = 0;
+    for (int64_t w : work) need += w > 0;
+    if ((int)g < need) g = (unsigned)need;
+    int64_t total = work[0] + work[1] + work[2];
+    int left = (int)g;
+    for (int k = 0; k < 3; k++) {
+        if (work[k] == 0) {
+            ctas[k] = 0;
+            continue;
+        }
+        int later = 0;  // groups after this one that still need a CTA
+        for (int q = k + 1; q < 3; q++) later += work[q] > 0;
+        int c = (int)std::max<int64_t>(1, (int64_t)g * work[k] / std::max<int64_t>(1, total));
+        c = std::min(c, left - later);
+        if (later == 0) c = left;
+        ctas[k] = c;
+        left -= c;
+    }
+}
+
+template <int T>
+cudaError_t v7_launch(unsigned g, const float *src, float *dst, int nz, int ny, int nx, float r,
+                      cudaStream_t s) {
+    constexpr size_t smem = v4_smem_bytes<T>();
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_optin(k_heat3d_v7<T>, (int)smem, attr);
+    if (e != cudaSuccess) return e;
+    Tiling3 tl = tiling3(ny, nx, T);
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    // TMA needs 16-byte row strides and base, and every tile's x origin
+    // i*(64 - 2T) - T a multiple of 4 floats (16 bytes): T = 4 only; the tile
+    // must lie inside the field
+    constexpr bool aligned_origins = (64 - 2 * T) % 4 == 0 && T % 4 == 0;
+    if (aligned_origins && enc && nx % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0) {
+        interior3(nx, tl.fx, T, &tl.ia, &tl.nix);
+        interior3(ny, tl.fy, T, &tl.ja, &tl.niy);
+        if (tl.nix > 0 && tl.niy > 0) {
+            const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+            const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+            const cuuint32_t box[3] = {64, 64, 1}, estr[3] = {1, 1, 1};
+            if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(src), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                tl.nix = tl.niy = 0;
+        } else {
+            tl.nix = tl.niy = 0;
+        }
+    }
+    tl.ne = tl.ff - tl.nix * tl.niy;
+    const int64_t work[3] = {(int64_t)tl.nix * tl.niy, (int64_t)tl.ne + tl.fn,
+                             (int64_t)tl.nf + tl.nn};
+    int ctas[3];
+    split_ctas(g, work, ctas);
+    tl.ctas_tma = ctas[0];
+    tl.ctas_wide = ctas[0] + ctas[1];
+    k_heat3d_v7<T><<<g, V3_NW * 32, smem, s>>>(src, dst, nz, ny, nx, r, tl, map);
     return cudaGetLastError();
 }
 
@@ -930,8 +1217,16 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
             return cudaErrorInvalidValue;
         const int BX = 64 - 2 * steps, BY = V3_H - 2 * steps;
         int64_t work = (int64_t)((nx + BX - 1) / BX) * ((ny + BY - 1) / BY) * nz;
-        if (variant == 6) work = v6_units(ny, nx, steps) * nz;
+        if (variant >= 6) work = v6_units(ny, nx, steps) * nz;
         const unsigned g3 = cfg ? g : (unsigned)std::min<int64_t>(sm_count(), work);
+        if (variant == 7) {
+            switch (steps) {
+                case 1: return v7_launch<1>(g3, src, dst, nz, ny, nx, r, s);
+                case 2: return v7_launch<2>(g3, src, dst, nz, ny, nx, r, s);
+                case 3: return v7_launch<3>(g3, src, dst, nz, ny, nx, r, s);
+                case 4: return v7_launch<4>(g3, src, dst, nz, ny, nx, r, s);
+            }
+        }
         if (variant == 6) {
             switch (steps) {
                 case 1: return v6_launch<1>(g3, src, dst, nz, ny, nx, r, s);
@@ -963,6 +1258,17 @@ cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r
         case 4: k_heat3d_pk<4><<<g, NT, 0, s>>>(src, dst, nz, ny, nx, r, zchunk); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t heat3d_wait_errors(unsigned *flags) {
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_heat3d_wait_errors, sizeof v);
+    if (e == cudaSuccess && v) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_heat3d_wait_errors, &zero, sizeof zero);
+    }
+    if (flags) *flags = v;
+    return e;
 }
 
 }  // namespace k

@@ -90,6 +90,9 @@ size_t tile_norm_grid_scratch_bytes(int64_t tiles);
 cudaError_t heat3d(const float *src, float *dst, int nz, int ny, int nx, float r, int steps,
                    int zchunk, const hxc_launch_cfg *cfg, cudaStream_t s);
 int heat3d_default_zchunk(int nz, int ny, int nx, int T);
+// Reads and clears the record of 3D launches whose bounded waits ran out
+// (form 7's TMA barriers); synchronous.
+cudaError_t heat3d_wait_errors(unsigned *flags);
 
 // Variable-diffusivity step (coefficients precomputed by vc_coef or on the
 // fly), adjoint step with kappa-gradient, squared-error seed, batches.

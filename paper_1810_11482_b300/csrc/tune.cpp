@@ -29,8 +29,8 @@ Knob g_knobs[] = {
     {"heat2d.rows", 16, 1, 4096},     // rows per warp of the 2D kernel
     {"heat2d.occupancy", 4, 4, 6},    // compiled minimum of CTAs per SM
     {"heat3d.zchunks", 0, 0, 64},     // z chunks per launch of form 2 (0: fill whole waves)
-    {"heat3d.variant", 6, 2, 6},      // 2 three-plane, 3 two-plane, 4 + ring, 6 + packed narrow tiles
-    {"heat3d.variant1", 5, 2, 6},     // the same choice for one-step launches, 5 = streaming one-step kernel
+    {"heat3d.variant", 6, 2, 7},      // 2 three-plane, 3 two-plane, 4 + ring, 6 + packed narrow tiles, 7 + TMA
+    {"heat3d.variant1", 5, 2, 7},     // the same choice for one-step launches, 5 = streaming one-step kernel
     {"heat1d.tb_ctas", 0, 0, 1 << 16},  // CTAs per partition of the 1D blocked kernel (0: SMs/parts)
     {"heat1d.steps_per_launch", 0, 0, 1024},  // fused 1D steps per launch when the caller passes 0 (0: all)
     {"heat3d.steps_per_launch", 4, 1, 4},     // fused 3D steps per launch when the caller passes 0

@@ -256,6 +256,7 @@ _SIGS = {
     "hxc_tune_load": (c_st, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int]),
     "hxc_tile_norms_noalloc": (c_st, [ctypes.c_void_p, i64, i64, i64, i64, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    "hxc_debug_wait_errors": (c_st, [c_dev, ctypes.POINTER(ctypes.c_uint32)]),
     "hxc_pipe_rate": (c_st, [c_dev, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
     "hxc_heat2d_run_host": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p,
@@ -678,6 +679,14 @@ def host_empty(shape, dtype=np.float64):
     if isinstance(shape, int):
         shape = (shape,)
     return np.asarray(_Pinned(shape, np.dtype(dtype)))
+
+
+def debug_wait_errors(dev):
+    """Reads and clears the record of device-side bounded waits that ran out
+    (0: none)."""
+    v = ctypes.c_uint32()
+    check(lib().hxc_debug_wait_errors(dev.h, ctypes.byref(v)), "debug_wait_errors")
+    return int(v.value)
 
 
 def pipe_rate(dev, kind):

@@ -271,6 +271,14 @@ def test_debug_inject_arguments():
     hxc.debug_inject(-1)
 
 
+def test_debug_wait_errors_arguments(L):
+    """hxc_debug_wait_errors rejects a NULL output and an invalid device
+    before touching any device."""
+    flags = ctypes.c_uint32()
+    assert L.hxc_debug_wait_errors(None, None) == hxc.HXC_E_INVALID
+    assert L.hxc_debug_wait_errors(None, ctypes.byref(flags)) == hxc.HXC_E_INVALID
+
+
 def test_host_run_and_graph_calls_reject_bad_arguments(L):
     """Argument checks of the host-memory run entry points and the graph
     calls come before any device work, so they hold without a GPU."""

@@ -80,7 +80,7 @@ def test_heat3d_translation_and_reflection_exact(dev):
                               dtype=np.float32)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1")}
     try:
-        for variant in (2, 3, 4, 6):
+        for variant in (2, 3, 4, 6, 7):
             hxc.tune_set("heat3d.variant", variant)
             hxc.tune_set("heat3d.variant1", variant)
             ref, _ = run3d(dev, u0, 8, "fused", 4)
@@ -109,7 +109,7 @@ def test_heat3d_kernel_variants_and_zchunks_bitexact(dev, shape):
     want = oracle.heat3d(u0.astype(np.float64), float(R), 9)
     old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1", "heat3d.zchunks")}
     try:
-        for variant in (2, 3, 4, 6):
+        for variant in (2, 3, 4, 6, 7):
             hxc.tune_set("heat3d.variant", variant)
             hxc.tune_set("heat3d.variant1", variant)
             for nch in (0, 1, 3):
@@ -190,7 +190,7 @@ def test_heat3d_full_size_windows(dev):
     # every two-plane form gives these bits at full size too
     old = hxc.tune_get("heat3d.variant")
     try:
-        for variant in (3, 4, 6):
+        for variant in (3, 4, 6, 7):
             hxc.tune_set("heat3d.variant", variant)
             other, _ = run3d(dev, u0, 200, "fused", 4)
             assert np.array_equal(other, got), variant
@@ -225,7 +225,8 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
             want = None
             for variant, grid in ((2, None), (3, None), (3, 1), (3, 7), (3, 150), (3, 100000),
                                   (4, None), (4, 1), (4, 7), (4, 100000), (6, None), (6, 1),
-                                  (6, 7), (6, 100000)):
+                                  (6, 7), (6, 100000), (7, None), (7, 1), (7, 7),
+                                  (7, 100000)):
                 hxc.tune_set("heat3d.variant", variant)
                 hxc.tune_set("heat3d.variant1", variant)
                 a.write(u0).get()
@@ -245,6 +246,50 @@ def test_heat3d_two_plane_form_any_grid(dev, shape):
         args = hxc.hxc_heat3d_args(a.h, b.h, shape[0], shape[1], shape[2], R, 4)
         with pytest.raises(hxc.HxcError):
             dev.launch(hxc.HXC_K_HEAT3D, args, cfg=hxc.hxc_launch_cfg((4, 1, 1), (256, 1, 1))).get()
+    finally:
+        for k, v in old.items():
+            hxc.tune_set(k, v)
+
+
+@pytest.mark.parametrize("shape", [(12, 200, 232), (5, 130, 176)])
+def test_heat3d_tma_form(dev, shape):
+    """Form 7 fetches the input planes of the regions inside the field with
+    TMA tensor copies (4 steps per launch, nx % 4 == 0): on fields with
+    several such regions in x and y, edge and narrow regions beside them and a
+    z extent smaller than the launch's reach, every grid (fewer CTAs than
+    tile kinds, a few, more CTAs than work) gives the bits of form 6 for 1..4
+    steps per launch, and no bounded wait ran out."""
+    u0 = np.ascontiguousarray(synth.heat3d_input(shape[2], seed=370 + shape[0], nz=shape[0],
+                                                 ny=shape[1]), dtype=np.float32)
+    old = {k: hxc.tune_get(k) for k in ("heat3d.variant", "heat3d.variant1")}
+    a, b = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    hxc.debug_wait_errors(dev)
+    try:
+        for steps in (4, 3, 2, 1):
+            want = None
+            for variant, grid in ((6, None), (7, None), (7, 1), (7, 2), (7, 7), (7, 100000)):
+                hxc.tune_set("heat3d.variant", variant)
+                hxc.tune_set("heat3d.variant1", variant)
+                a.write(u0).get()
+                args = hxc.hxc_heat3d_args(a.h, b.h, shape[0], shape[1], shape[2], R, steps)
+                cfg = None if grid is None else hxc.hxc_launch_cfg((grid, 1, 1), (512, 1, 1))
+                dev.launch(hxc.HXC_K_HEAT3D, args, cfg=cfg).get()
+                got = np.empty_like(u0)
+                b.read_sync(got)
+                if want is None:
+                    want = got
+                    ora = oracle.heat3d(u0.astype(np.float64), float(R), steps)
+                    assert relerr(got, ora) <= TOL32
+                else:
+                    assert np.array_equal(got, want), (steps, variant, grid)
+        # whole runs of several launches in every mode
+        hxc.tune_set("heat3d.variant", 6)
+        ref, _ = run3d(dev, u0, 13, "fused", 4)
+        hxc.tune_set("heat3d.variant", 7)
+        for mode in ("fused", "graph"):
+            got, _ = run3d(dev, u0, 13, mode, 4)
+            assert np.array_equal(got, ref), mode
+        assert hxc.debug_wait_errors(dev) == 0
     finally:
         for k, v in old.items():
             hxc.tune_set(k, v)
