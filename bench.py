@@ -510,7 +510,7 @@ def secondary(dev, timer, peaks):
     res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": gbs / peaks["hbm_gbs"], "ms_per_launch": launch_ms,
                        "traffic": traffic3,
-                       "kernel": "k_heat3d_v6<4> (4 steps of the whole 512^3 field per launch, packed narrow tiles)",
+                       "kernel": "k_heat3d_v7<4> (4 steps of the whole 512^3 field per launch, packed narrow tiles, TMA-fed interior regions)",
                        "effective_gbs_1step_equiv": 2 * u3.nbytes * st3 / (res["fused"]["ms"] / 1e3) / 1e9}
     # the one-step launches of plain mode (streaming kernel): read + write once per step
     ms1 = res["plain"]["ms"] / st3
