@@ -40,10 +40,12 @@ TILES = (8, 8)
 R2D = 0.2
 STEPS2D = 1000
 EVERY = 100
-# FP64 pipe operations of one 2D update in the pair-sum form: its own
-# anti-diagonal pair sum (the other one is shared with the point up-left),
-# the sum of the two pair sums, and 2 fused multiply-adds
-OPS_PER_UPDATE_2D = 4
+# FP64 pipe operations of one 2D update in the pair-sum form, by step kind
+# (canonical, scaled, closing; hxc_heat2d_step_kinds): its own anti-diagonal
+# pair sum (the other one is shared with the point up-left), the sum of the
+# two pair sums, then 2 fused multiply-adds (canonical), 1 (scaled), or a
+# product and a fused multiply-add (closing)
+OPS_BY_KIND_2D = (4, 3, 4)
 BYTES_PER_UPDATE_2D = 16  # one 8-byte read and one 8-byte write
 
 
@@ -333,7 +335,9 @@ def ours(args, world, rank, local, pg):
     f, st = hxc.heat2d_run(dev, u, tmp, cfg, deps=[start])
     kms = timer.stop(f) / rsteps
     upd_launch = NY * NX
-    ach_gops = upd_launch * OPS_PER_UPDATE_2D / (kms / 1e3) / 1e9
+    kinds = hxc.heat2d_step_kinds(cfg)
+    ops_upd = sum(n * o for n, o in zip(kinds, OPS_BY_KIND_2D)) / float(sum(kinds))
+    ach_gops = upd_launch * ops_upd / (kms / 1e3) / 1e9
     ach_gbs = upd_launch * BYTES_PER_UPDATE_2D / (kms / 1e3) / 1e9
     traffic = None
     tp = os.path.join(HERE, "profiles", "heat2d_traffic.json")
@@ -341,7 +345,11 @@ def ours(args, world, rank, local, pg):
         traffic = json.load(open(tp)).get("bytes_per_launch")
     roof = {"bound": "alu", "achieved": ach_gops, "peak": peaks["fp64_gops"], "unit": "Gop/s",
             "frac": ach_gops / peaks["fp64_gops"], "traffic": traffic,
-            "kernel": "k_heat2d<2> (whole 8192^2 field, one step per launch, 4 FP64 ops/update)",
+            "kernel": "k_heat2d<2> (whole 8192^2 field, one step per launch, %.3f FP64 "
+                      "ops/update: %d scaled steps of 3, %d closing steps of 4)"
+                      % (ops_upd, kinds[1], kinds[2] + kinds[0]),
+            "ops_per_update": ops_upd, "step_kinds": {"canonical": kinds[0], "scaled": kinds[1],
+                                                      "closing": kinds[2]},
             "ms_per_launch": kms,
             "peak_source": peaks["fp64_source"], "nominal_peak": peaks["fp64_nominal_gops"],
             "frac_of_nominal": ach_gops / peaks["fp64_nominal_gops"],

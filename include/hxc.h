@@ -472,7 +472,10 @@ typedef struct {
  * issued one at a time (they share the device's snapshot rings and norm
  * rows): a run called while another thread issues one is queued and issued
  * by that thread right after, without blocking the caller (stats again
- * count nothing; errors then reach *out instead of the return value). */
+ * count nothing; errors then reach *out instead of the return value).
+ * The steps' arithmetic is given under hxc_heat2d_step_kinds; it depends
+ * on the step's index only, so results are bit-identical for every tile
+ * grid and mode. */
 hxc_status hxc_heat2d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, const hxc_heat2d_cfg *cfg,
                           const hxc_future *deps, int ndeps, hxc_future *out,
                           hxc_future *field_ready, hxc_run_stats *stats);
@@ -500,6 +503,24 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dev, const double *host_u0, doub
                                      const hxc_heat2d_cfg *cfg, const hxc_future *deps,
                                      int ndeps, hxc_future *out, hxc_run_stats *stats);
 
+/* Step kinds of a 2D run (hxc_heat2d_run and its host forms; the streamed
+ * run of the same steps without snapshots).  FTCS is linear,
+ * u_{n+1} = r ((1 - 4r)/r u_n + s(u_n)) with s the four neighbours' sum, so
+ * the runs carry the field scaled by r^-m after m steps and advance it with
+ * one FMA after the sum: counts[1] "scaled" steps, v' = fma((1-4r)/r, v, s),
+ * 3 FP64 operations per point; counts[2] "closing" steps back to true
+ * values, u' = fma(r^(m+1), s, ((1-4r) r^m) v), 4 operations; counts[0]
+ * canonical steps, t = fma(-4, u, s), u' = fma(r, t, u), 4 operations (every
+ * step when r is outside (0, 1/4] or r^-1 > 2^48).  s is always
+ * (uN + uW) + (uE + uS).  The steps are issued in intervals (snapshot_every
+ * when snapshot norms are requested, else min(steps, 100)); each interval is
+ * cut into groups of at most M + 1 steps, M the largest m with r^-m <= 2^48
+ * (20 at r = 0.2), whose last step closes, so the field holds true values at
+ * every snapshot and at the end.  The scaled field grows by at most 1/r per
+ * step: inputs with |u| <= 2^975 stay finite.  counts: 3 int64 written.
+ * Host only, no device needed. */
+hxc_status hxc_heat2d_step_kinds(const hxc_heat2d_cfg *cfg, int64_t *counts);
+
 /* 3D periodic FTCS in FP32 on an nz x ny x nx field (x fastest): u holds
  * the initial field and receives the result, tmp is scratch of the same
  * size.  PLAIN launches one step at a time, FUSED advances
@@ -511,7 +532,7 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dev, const double *host_u0, doub
  * hxc_heat2d_run) as a call of its own: out[i] = sqrt(sum of squares) of
  * the counts[i] doubles at arrays[i], one task per array on the worker
  * pool, in the same summation order as the run's continuations (blocks of
- * 1024 squares over 8 accumulators, block sums pairwise).  Synchronous. */
+ * 64 squares over 8 accumulators, block sums pairwise).  Synchronous. */
 hxc_status hxc_host_norms(const double *const *arrays, const int64_t *counts, int n, double *out);
 
 /* The 2D run with the field in host memory and every step streamed through

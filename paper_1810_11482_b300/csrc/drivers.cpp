@@ -16,6 +16,7 @@
 #include <memory>
 
 #include "drivers_util.hpp"
+#include "ftcs2_plan.hpp"
 #include "kernels.cuh"
 #include "tune.hpp"
 #include "runtime.hpp"
@@ -331,7 +332,8 @@ struct Heat2dRun {
     Stats stats;
 };
 
-// Issues steps [s0, s1) of the per-tile plain schedule.
+// Issues steps [s0, s1), one interval of the run (its step kinds follow
+// ftcs2_step), per tile or fused.
 hxc_status issue_steps2d(Heat2dRun &R, int64_t s0, int64_t s1, std::vector<FutRef> &prev,
                          bool fused) {
     const hxc_heat2d_cfg &c = *R.cfg;
@@ -339,16 +341,16 @@ hxc_status issue_steps2d(Heat2dRun &R, int64_t s0, int64_t s1, std::vector<FutRe
     for (int64_t s = s0; s < s1; s++) {
         const double *src = R.buf[s % 2];
         double *dst = R.buf[(s + 1) % 2];
+        const k::Ftcs2Step kind = ftcs2_step(c.r, s - s0, s1 - s0);
         if (fused) {
             std::vector<FutRef> deps;
             for (auto &f : prev)
                 if (f) deps.push_back(f);
             FutRef f;
             int64_t ny = c.ny, nx = c.nx;
-            double r = c.r;
             hxc_status st = issue_device_op(
                 R.dev, 0, deps,
-                [=](cudaStream_t st) { return k::heat2d(src, dst, ny, nx, 0, 0, ny, nx, r, 0, nullptr, st); },
+                [=](cudaStream_t st) { return k::heat2d_step(src, dst, ny, nx, 0, 0, ny, nx, kind, 0, st); },
                 {}, &f);
             if (st) return st;
             R.stats.launch();
@@ -362,10 +364,9 @@ hxc_status issue_steps2d(Heat2dRun &R, int64_t s0, int64_t s1, std::vector<FutRe
                 if (prev[q]) deps.push_back(prev[q]);
             int64_t ny = c.ny, nx = c.nx, y0 = R.tl.y0(t), x0 = R.tl.x0(t), ty = R.tl.ty(t),
                     tx = R.tl.tx(t);
-            double r = c.r;
             hxc_status st = issue_device_op(
                 R.dev, (int)t, deps,
-                [=](cudaStream_t st) { return k::heat2d(src, dst, ny, nx, y0, x0, ty, tx, r, 0, nullptr, st); },
+                [=](cudaStream_t st) { return k::heat2d_step(src, dst, ny, nx, y0, x0, ty, tx, kind, 0, st); },
                 {}, &cur[t]);
             if (st) return st;
             R.stats.launch();
@@ -775,7 +776,7 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
     const bool fused = cfg->mode == HXC_MODE_FUSED;
     // without snapshots the steps are issued (and captured) in intervals of
     // at most 100 steps, which bounds the size of a captured graph
-    const int64_t every = want_snaps ? cfg->snapshot_every : std::min<int64_t>(cfg->steps, 100);
+    const int64_t every = heat2d_interval(*cfg);
     // the earlier runs' readers of the rings order this run's writes into them
     // but must not pass on their own failures: an unrelated later run would
     // otherwise fail with HXC_E_DEP_FAILED after one failed run
@@ -1132,6 +1133,15 @@ hxc_status hxc_heat2d_run_host(hxc_device dh, const double *host_u0, double *hos
     return st;
 }
 
+
+hxc_status hxc_heat2d_step_kinds(const hxc_heat2d_cfg *cfg, int64_t *counts) {
+    if (!cfg || !counts || cfg->steps < 0 || cfg->snapshot_every < 0) {
+        set_error("hxc_heat2d_step_kinds: invalid arguments");
+        return HXC_E_INVALID;
+    }
+    ftcs2_count(cfg->r, cfg->steps, heat2d_interval(*cfg), counts);
+    return HXC_OK;
+}
 
 hxc_status hxc_host_norms(const double *const *arrays, const int64_t *counts, int n, double *out) {
     if (n < 0 || (n > 0 && (!arrays || !counts || !out))) {

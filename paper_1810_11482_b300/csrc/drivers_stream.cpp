@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "drivers_util.hpp"
+#include "ftcs2_plan.hpp"
 #include "kernels.cuh"
 #include "runtime.hpp"
 
@@ -32,7 +33,6 @@ struct StreamPlan {
     int64_t ny, nx, TY, TX, H, W;
     std::vector<int64_t> by, bx;
     double *base;  // 2 * T buffers of H * W doubles
-    double r;
     int64_t count() const { return TY * TX; }
     double *in(int64_t t) const { return base + (size_t)t * H * W; }
     double *out(int64_t t) const { return base + (size_t)(count() + t) * H * W; }
@@ -40,7 +40,7 @@ struct StreamPlan {
 
 // Copy in, step, copy out of tile t from src to dst (host arrays).
 cudaError_t tile_step(const StreamPlan &pl, int64_t t, const double *src, double *dst,
-                      cudaStream_t s) {
+                      const k::Ftcs2Step &kind, cudaStream_t s) {
     const int64_t p = t / pl.TX, q = t % pl.TX;
     const int64_t y0 = pl.by[p], y1 = pl.by[p + 1], x0 = pl.bx[q], x1 = pl.bx[q + 1];
     const int64_t r0 = std::max<int64_t>(y0 - 1, 0), r1 = std::min<int64_t>(y1 + 1, pl.ny);
@@ -50,7 +50,7 @@ cudaError_t tile_step(const StreamPlan &pl, int64_t t, const double *src, double
                                       src + r0 * pl.nx + c0, pl.nx * 8, (c1 - c0) * 8, r1 - r0,
                                       cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    e = k::heat2d(in, out, (y1 - y0) + 2, pl.W, 1, 2, y1 - y0, x1 - x0, pl.r, 0, nullptr, s);
+    e = k::heat2d_step(in, out, (y1 - y0) + 2, pl.W, 1, 2, y1 - y0, x1 - x0, kind, 0, s);
     if (e != cudaSuccess) return e;
     return cudaMemcpy2DAsync(dst + y0 * pl.nx + x0, pl.nx * 8, out + pl.W + 2, pl.W * 8,
                              (x1 - x0) * 8, y1 - y0, cudaMemcpyDeviceToHost, s);
@@ -82,7 +82,6 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
     pl.nx = nx;
     pl.TY = tiles_y;
     pl.TX = tiles_x;
-    pl.r = r;
     pl.by = split(ny, tiles_y, false);
     pl.bx = split(nx, tiles_x, true);
     int64_t mty = 0, mtx = 0;
@@ -96,6 +95,13 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
     if ((st = d->scratch_get("heat2d_stream", bytes, &base))) return st;
     pl.base = static_cast<double *>(base);
     Stats sc{stats};
+    // the step kinds of the device-resident run without snapshots
+    // (intervals of at most 100 steps), so that both give the same bits
+    const int64_t every = std::min<int64_t>(steps, 100);
+    auto step_kind = [every, steps, r](int64_t step) {
+        const int64_t s0 = step / every * every;
+        return ftcs2_step(r, step - s0, std::min<int64_t>(every, steps - s0));
+    };
     auto count_step = [&]() {
         for (int64_t t = 0; t < T; t++) {
             const int64_t p = t / pl.TX, q = t % pl.TX;
@@ -117,8 +123,9 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
         for (int step = 0; step < steps && e == cudaSuccess; step++) {
             const double *src = step % 2 ? host_b : host_a;
             double *dst = step % 2 ? host_a : host_b;
+            const k::Ftcs2Step kind = step_kind(step);
             for (int64_t t = 0; t < T && e == cudaSuccess; t++) {
-                e = tile_step(pl, t, src, dst, s);
+                e = tile_step(pl, t, src, dst, kind, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             }
             count_step();
@@ -140,6 +147,7 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
     for (int step = 0; step < steps; step++) {
         const double *src = step % 2 ? host_b : host_a;
         double *dst = step % 2 ? host_a : host_b;
+        const k::Ftcs2Step kind = step_kind(step);
         for (int64_t t = 0; t < T; t++) {
             std::vector<FutRef> deps_t;
             if (step == 0) {
@@ -151,8 +159,8 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
                         deps_t.push_back(prev[a * pl.TX + b]);
             }
             if ((st = issue_device_op(d.get(), (int)t, deps_t,
-                                      [pp, t, src, dst](cudaStream_t s) {
-                                          return tile_step(*pp, t, src, dst, s);
+                                      [pp, t, src, dst, kind](cudaStream_t s) {
+                                          return tile_step(*pp, t, src, dst, kind, s);
                                       },
                                       {}, &cur[t])))
                 return st;

@@ -1,7 +1,7 @@
 // Core kernels: Listing 2 sum, PRK stencil, partition kernel, 1D and 2D
 // FTCS steps and the tile snapshot/norm reduction.
 //
-// Canonical arithmetic.  Every kernel variant (per-step, temporally blocked,
+// Fixed arithmetic.  Every kernel variant (per-step, temporally blocked,
 // any tile shape, any launch order) evaluates one update with exactly the
 // same sequence of correctly rounded FP64 operations, so results are
 // bit-identical across partition counts, schedules and graph replay:
@@ -13,6 +13,13 @@
 // computed once and used by two points (4 FP64 operations per point).  The
 // sums are symmetric under transposition and under a half turn, so
 // transposed or reversed inputs give transposed or reversed bits.
+//
+// The 2D runs use two more step kinds of the same sums (kernels.cuh): FTCS
+// is linear, so u_{n+1} = r ((1 - 4r)/r u_n + s(u_n)), and the field scaled
+// by r^-m after m steps advances by one FMA after the sum (3 operations per
+// point); a closing step takes the scaled field back to true values.  Which
+// step of a run is which kind depends only on the step's index, so the bit-
+// identity across partitions, schedules and graph replay holds for them too.
 #include "fp64_int.cuh"
 #include "kernels.cuh"
 #include "tune.hpp"
@@ -73,12 +80,21 @@ __device__ __forceinline__ double pair2(double a, double b, double one) {
 // The 2D update from the point's two pair sums, pNW = uN + uW and
 // pSE = uE + uS; their sum on the integer-pipe adder when E >= 2.  Every E
 // gives the same bits; the split balances the FP64 pipe against the
-// integer pipe.
-template <int E>
-__device__ __forceinline__ double ftcs5p(double u, double pNW, double pSE, double r, double one) {
+// integer pipe.  M is the step kind (kFtcs2Canon / Scaled / Close): the
+// scaled step is one FMA after the sum, so a scaled run costs 3 FP64
+// operations per point instead of 4.
+template <int E, int M>
+__device__ __forceinline__ double ftcs5p(double u, double pNW, double pSE, double c0, double c1,
+                                         double one) {
     const double s = E >= 2 ? dadd_int(pNW, pSE) : addf(pNW, pSE, one);
-    const double t = __fma_rn(-4.0, u, s);
-    return __fma_rn(r, t, u);
+    if constexpr (M == kFtcs2Scaled) {
+        return __fma_rn(c0, u, s);
+    } else if constexpr (M == kFtcs2Close) {
+        return __fma_rn(c0, s, __dmul_rn(c1, u));
+    } else {
+        const double t = __fma_rn(-4.0, u, s);
+        return __fma_rn(c0, t, u);
+    }
 }
 
 // ------------------------------------------------------------ Listing 2 sum
@@ -250,11 +266,11 @@ __device__ __forceinline__ double at2(const double *__restrict__ src, int64_t ny
     return (y >= 0 && y < ny && x >= 0 && x < nx) ? __ldg(src + y * nx + x) : 0.0;
 }
 
-template <int V, int EA, int EB, int MINB>
+template <int V, int EA, int EB, int MINB, int M>
 __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__ src,
                                                 double *__restrict__ dst, int64_t ny, int64_t nx,
                                                 int64_t y0, int64_t x0, int64_t ty, int64_t tx,
-                                                double r, int H, double one) {
+                                                double c0, double c1, int H, double one) {
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t SW = 32 * V;
@@ -305,15 +321,15 @@ __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__
                     const double q1 = pair2<EB>(rgt, nxt.b, one);
                     if (active) {
                         double2 o;
-                        o.x = ftcs5p<EA>(cur.a, pnw, q0, r, one);
-                        o.y = ftcs5p<EB>(cur.b, pp0, q1, r, one);
+                        o.x = ftcs5p<EA, M>(cur.a, pnw, q0, c0, c1, one);
+                        o.y = ftcs5p<EB, M>(cur.b, pp0, q1, c0, c1, one);
                         *reinterpret_cast<double2 *>(dst + y * nx + xl) = o;
                     }
                     pp0 = q0;
                     pp1 = q1;
                 } else {
                     const double q0 = pair2<EA>(rgt, nxt.a, one);
-                    if (active) dst[y * nx + xl] = ftcs5p<EA>(cur.a, pnw, q0, r, one);
+                    if (active) dst[y * nx + xl] = ftcs5p<EA, M>(cur.a, pnw, q0, c0, c1, one);
                     pp0 = q0;
                 }
                 eR = eRn;
@@ -331,9 +347,12 @@ void set_heat2d_rows(int v) { tune::set("heat2d.rows", v); }
 int heat2d_occupancy() { return (int)tune::get("heat2d.occupancy"); }
 void set_heat2d_occupancy(int v) { tune::set("heat2d.occupancy", v); }
 
-cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
-                   int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
-                   const hxc_launch_cfg *cfg, cudaStream_t s) {
+namespace {
+
+template <int M>
+cudaError_t heat2d_launch(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
+                          int64_t x0, int64_t ty, int64_t tx, double c0, double c1,
+                          int rows_per_warp, const hxc_launch_cfg *cfg, cudaStream_t s) {
     if (ty <= 0 || tx <= 0) return cudaSuccess;
     const int H = rows_per_warp > 0 ? rows_per_warp : heat2d_rows();
     const bool vec = (nx % 2 == 0) && (x0 % 2 == 0) && (tx % 2 == 0) &&
@@ -347,7 +366,8 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
     // (0..4: points a and b of a lane take floor/ceil of half of it), and
     // the minimum resident CTAs per SM the kernel is compiled for (4..6)
     const int em = heat2d_emul(), occ = heat2d_occupancy();
-#define HXC_L2D(VV, A, B, M) k_heat2d<VV, A, B, M><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, r, H, 1.0)
+#define HXC_L2D(VV, A, B, MB) \
+    k_heat2d<VV, A, B, MB, M><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, c0, c1, H, 1.0)
     if (!vec) {
         switch (em / 2) {
             case 0: HXC_L2D(1, 0, 0, 4); break;
@@ -372,6 +392,31 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
     }
 #undef HXC_L2D
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
+                   int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
+                   const hxc_launch_cfg *cfg, cudaStream_t s) {
+    return heat2d_launch<kFtcs2Canon>(src, dst, ny, nx, y0, x0, ty, tx, r, 0.0, rows_per_warp,
+                                      cfg, s);
+}
+
+cudaError_t heat2d_step(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
+                        int64_t x0, int64_t ty, int64_t tx, const Ftcs2Step &step,
+                        int rows_per_warp, cudaStream_t s) {
+    switch (step.kind) {
+        case kFtcs2Scaled:
+            return heat2d_launch<kFtcs2Scaled>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
+                                               rows_per_warp, nullptr, s);
+        case kFtcs2Close:
+            return heat2d_launch<kFtcs2Close>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
+                                              rows_per_warp, nullptr, s);
+        default:
+            return heat2d_launch<kFtcs2Canon>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
+                                              rows_per_warp, nullptr, s);
+    }
 }
 
 // ------------------------------------------------------ tile snapshot/norm

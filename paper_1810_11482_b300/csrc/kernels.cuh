@@ -54,10 +54,25 @@ cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_
 constexpr int kHeat1dMaxSteps = 1024;
 
 // One 2D FTCS step of the tile [y0, y0+ty) x [x0, x0+tx); rows_per_warp <= 0
-// picks the default.
+// picks the default.  Canonical arithmetic (true values in and out).
 cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
                    const hxc_launch_cfg *cfg, cudaStream_t s);
+
+// Kinds of 2D step.  With s = (uN + uW) + (uE + uS) of the values read:
+//   kFtcs2Canon  (c0 = r):           t = fma(-4, u, s); u' = fma(r, t, u)
+//   kFtcs2Scaled (c0 = (1 - 4r)/r):  u' = fma(c0, u, s)
+//   kFtcs2Close  (c0, c1):           u' = fma(c0, s, c1 * u)
+// A scaled step maps v = u_n / r^m to u_{n+1} / r^(m+1); a closing step
+// with c0 = r^(m+1), c1 = (1 - 4r) r^m maps v = u_n / r^m to u_{n+1}.
+enum : int { kFtcs2Canon = 0, kFtcs2Scaled = 1, kFtcs2Close = 2 };
+struct Ftcs2Step {
+    int kind;
+    double c0, c1;
+};
+cudaError_t heat2d_step(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
+                        int64_t x0, int64_t ty, int64_t tx, const Ftcs2Step &step,
+                        int rows_per_warp, cudaStream_t s);
 
 // 2D kernel knobs (tuning registry): share of the additions run on the
 // integer pipe (half-additions per point, 0..6), rows per warp, compiled

@@ -295,3 +295,37 @@ def test_host_run_and_graph_calls_reject_bad_arguments(L):
     g = hxc.c_graph()
     assert L.hxc_graph_end(bogus, ctypes.byref(g)) == hxc.HXC_E_INVALID
     assert L.hxc_graph_launch(bogus, 0, None, 0, ctypes.byref(out)) == hxc.HXC_E_INVALID
+
+
+@pytest.mark.parametrize("r,steps,every,norms,want", [
+    # r = 0.2: at most 20 scaled steps in a row (0.2^-20 <= 2^48 < 0.2^-21), so
+    # an interval of 100 steps is 5 groups (4 x 21 + 16), each closed once
+    (0.2, 1000, 100, True, (0, 950, 50)),
+    (0.2, 1000, 100, False, (0, 950, 50)),  # no norms: intervals of 100 all the same
+    (0.2, 200, 0, False, (0, 190, 10)),
+    (0.2, 22, 0, False, (0, 20, 2)),        # 21 + 1
+    (0.2, 21, 0, False, (0, 20, 1)),
+    (0.2, 1000, 1, True, (0, 0, 1000)),     # a snapshot after every step
+    (0.2, 10, 3, True, (0, 6, 4)),          # intervals 3, 3, 3 (2 scaled + 1) and a last 1
+    # r = 1/4: (1/4)^24 = 2^-48 exactly, so 24 scaled steps: 100 = 4 x 25
+    (0.25, 100, 0, False, (0, 96, 4)),
+    # r = 0.01: 7 (0.01^-7 = 1e14 <= 2^48 < 1e16): 250 = 100 + 100 + 50,
+    # 13 + 13 + 7 groups of at most 8
+    (0.01, 250, 0, False, (0, 217, 33)),
+    (0.3, 50, 0, False, (50, 0, 0)),        # beyond the stability bound: canonical
+    (1e-17, 10, 0, False, (10, 0, 0)),      # one scaled step would grow 1e17 > 2^48
+    (-0.1, 5, 0, False, (5, 0, 0)),
+    (0.2, 0, 0, False, (0, 0, 0)),
+])
+def test_heat2d_step_kinds(L, r, steps, every, norms, want):
+    """The 2D runs' schedule of scaled and closing steps (host only)."""
+    hn = np.zeros(max(1, steps // max(every, 1))) if norms else None
+    cfg = hxc.heat2d_cfg(64, 64, 1, 1, r, steps, every, "fused", hn, None)
+    assert hxc.heat2d_step_kinds(cfg) == want
+    assert sum(want) == steps
+
+
+def test_heat2d_step_kinds_arguments(L):
+    cfg = hxc.heat2d_cfg(64, 64, 1, 1, 0.2, -1, 0, "fused", None, None)
+    assert L.hxc_heat2d_step_kinds(ctypes.byref(cfg), (ctypes.c_int64 * 3)()) == hxc.HXC_E_INVALID
+    assert L.hxc_heat2d_step_kinds(None, (ctypes.c_int64 * 3)()) == hxc.HXC_E_INVALID

@@ -225,6 +225,37 @@ def test_heat2d_bitexact_across_tilings_and_modes(dev):
     assert np.array_equal(got, ref.T)
 
 
+@pytest.mark.parametrize("r", [0.2, 0.25, 0.1, 0.01, 1e-17])
+def test_heat2d_scaled_steps_vs_oracle(dev, r):
+    """The runs' scaled and closing steps (hxc_heat2d_step_kinds): 250 steps
+    without snapshots are three intervals (100, 100, 50), each cut into
+    groups that end in a closing step; r = 1e-17 runs canonical steps only.
+    Every mode and tiling gives the same bits, within the FP64 tolerance of
+    the oracle."""
+    u0 = synth.bumps2d(96, 130, seed=235, nbumps=5, sigma=0.1)
+    steps = 250
+    kinds = hxc.heat2d_step_kinds(hxc.heat2d_cfg(96, 130, 2, 3, r, steps, 0, "plain", None, None))
+    assert sum(kinds) == steps and (kinds[0] == steps) == (r == 1e-17)
+    want = oracle.heat2d(u0, r, steps)
+    ref, _, _, _ = run2d(dev, u0, (1, 1), r, steps, "fused")
+    assert relerr(ref, want) <= TOL
+    for tiles in ((2, 3), (4, 1)):
+        for mode in ("plain", "graph", "fused"):
+            got, _, _, _ = run2d(dev, u0, tiles, r, steps, mode)
+            assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), (tiles, mode)
+
+
+def test_heat2d_scaled_steps_large_magnitudes(dev):
+    """A field of magnitude 2^900: the scaled field reaches about 2^946
+    before each closing step (52 steps: groups of 21, 21 and 10) and stays
+    finite; the result is within the tolerance of the oracle."""
+    u0 = synth.bumps2d(64, 72, seed=236, nbumps=4, sigma=0.1) * 2.0 ** 900
+    want = oracle.heat2d(u0, 0.2, 52)
+    for mode in ("plain", "fused"):
+        got, _, _, _ = run2d(dev, u0, (2, 2), 0.2, 52, mode)
+        assert np.all(np.isfinite(got)) and relerr(got, want) <= TOL, mode
+
+
 def test_heat2d_rows_and_occupancy_knobs_bitexact(dev):
     """The strip height (rows per warp, including heights that are not
     multiples of the 32-row groups in which the strip-edge pair sums are

@@ -209,6 +209,59 @@ def _case_forward(dev, mode):
     return prepare, issue, result
 
 
+def _case_forward_tape(dev, mode):
+    """The forward that keeps its checkpoints (tape) for a later gradient."""
+    n, steps, every = 66, 27, 5
+    kref, kap, u0, c = synth.adjoint_input(n)
+    ns = hxc.varcoef_tape_states(steps, every)
+    b0, bk, ut = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    tape = dev.buffer(ns * u0.nbytes)
+    b0.write(u0).get()
+    bk.write(kap).get()
+
+    def prepare():
+        pass
+
+    def issue():
+        return hxc.varcoef_forward_tape(dev, b0, bk, n, n, c, steps, ut, tape, every)[0]
+
+    def result():
+        out, tp = np.empty_like(u0), np.empty(ns * n * n)
+        ut.read_sync(out)
+        tape.read_sync(tp)
+        return np.concatenate([out.ravel(), tp])
+    return prepare, issue, result
+
+
+def _case_adjoint_tape(dev, mode):
+    """The gradient that starts from a forward's checkpoints; the tape is
+    written once, before the runs under test, and is only read by them."""
+    n, steps, every = 60, 23, 6
+    kref, kap, u0, c = synth.adjoint_input(n)
+    ns = hxc.varcoef_tape_states(steps, every)
+    b0, bk, bl = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    ut, gk, gu = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    tape = dev.buffer(ns * u0.nbytes)
+    b0.write(u0).get()
+    bk.write(kap).get()
+    bl.write(u0).get()
+    f, _ = hxc.varcoef_forward_tape(dev, b0, bk, n, n, c, steps, ut, tape, every)
+    assert f.wait(WAIT_NS) == hxc.HXC_OK
+
+    def prepare():
+        pass
+
+    def issue():
+        return hxc.varcoef_adjoint_tape(dev, tape, bk, bl, n, n, c, steps, gk, gu, every, mode)[0]
+
+    def result():
+        a, b = np.empty_like(u0), np.empty_like(u0)
+        gk.read_sync(a)
+        gu.read_sync(b)
+        return np.concatenate([a.ravel(), b.ravel()])
+    return prepare, issue, result
+
+
 def _case_stream2d(dev, mode):
     u0 = synth.bumps2d(70, 90, seed=273, nbumps=3, sigma=0.1)
     ha, hb = hxc.host_empty(u0.shape), hxc.host_empty(u0.shape)
@@ -353,7 +406,9 @@ CASES = [("heat1d", _case_heat1d, m) for m in ("plain", "graph", "fused")] + \
         [("heat3d", _case_heat3d, m) for m in ("plain", "graph", "fused")] + \
         [("batch", _case_batch, m) for m in ("plain", "graph", "fused")] + \
         [("adjoint", _case_adjoint, m) for m in ("plain", "graph", "fused")] + \
-        [("forward", _case_forward, "fused"), ("stream2d", _case_stream2d, "plain"),
+        [("adjoint_tape", _case_adjoint_tape, m) for m in ("plain", "graph", "fused")] + \
+        [("forward", _case_forward, "fused"), ("forward_tape", _case_forward_tape, "fused"),
+         ("stream2d", _case_stream2d, "plain"),
          ("stream2d", _case_stream2d, "fused"), ("partition", _case_partition, "fused"),
          ("mandelbrot", _case_mandelbrot, "plain"), ("mandelbrot", _case_mandelbrot, "fused"),
          ("program", _case_program, "plain")]

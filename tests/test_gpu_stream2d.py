@@ -33,7 +33,7 @@ def streamed(dev, u0, tiles, r, steps, sequential, deps=()):
 
 @pytest.mark.parametrize("shape,tiles,steps", [((300, 302), (3, 4), 5), ((301, 257), (2, 3), 4),
                                                ((7, 9), (7, 3), 3), ((64, 64), (1, 1), 6),
-                                               ((130, 98), (4, 4), 1)])
+                                               ((130, 98), (4, 4), 1), ((64, 66), (2, 2), 45)])
 def test_streamed_matches_resident_and_oracle(dev, shape, tiles, steps):
     u0 = synth.bumps2d(*shape, seed=400 + shape[0], nbumps=6, sigma=0.1)
     want = run2d(dev, u0, (1, 1), 0.2, steps)[0]
