@@ -542,7 +542,7 @@ GnormStage &gnorm_stage(Device *d) {
 
 hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const hxc_heat2d_cfg *cfg,
                            std::vector<FutRef> dv, FutRef *all_out, FutRef *field_out,
-                           hxc_run_stats *stats_out);
+                           hxc_run_stats *stats_out, bool after_last_norms);
 
 // A 2D run reads and replaces state the device carries from run to run (the
 // last readers of the snapshot rings, the last copy of the device norm rows)
@@ -609,14 +609,12 @@ hxc_status issue_serial(Device *d, RunIssue later, RunIssue now, FutRef *all, Fu
     return st;
 }
 
-}  // namespace
-
-extern "C" {
-
-hxc_status hxc_heat2d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, const hxc_heat2d_cfg *cfg,
-                          const hxc_future *deps, int ndeps, hxc_future *out,
-                          hxc_future *field_ready, hxc_run_stats *stats_out) {
-    hxc::drv::NvtxRange nvtx_range("hxc_heat2d_run");
+// hxc_heat2d_run; after_last_norms orders the run after the previous 2D
+// run's device-norm copy (the host-memory entry points).
+hxc_status heat2d_run_entry(hxc_device dh, hxc_buffer uh, hxc_buffer th, const hxc_heat2d_cfg *cfg,
+                            const hxc_future *deps, int ndeps, hxc_future *out,
+                            hxc_future *field_ready, hxc_run_stats *stats_out,
+                            bool after_last_norms) {
     Ref<Device> d = dev_from_handle(dh);
     Ref<Buffer> u = buf_from_handle(uh), tb = buf_from_handle(th);
     if (!d || !u || !tb) return HXC_E_INVALID;
@@ -640,22 +638,23 @@ hxc_status hxc_heat2d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, const hxc
     if (stats_out) memset(stats_out, 0, sizeof *stats_out);
     FutRef a, b;
     auto c = std::make_shared<hxc_heat2d_cfg>(*cfg);
+    const bool aln = after_last_norms;
     if (has_pending_host(dv)) {
         defer_run(dv,
-                  [d, u, tb, c](FutRef *ia, FutRef *ib) {
-                      return issue_serial(d.get(), [d, u, tb, c](FutRef *ja, FutRef *jb) {
-                          return heat2d_run_impl(d, u, tb, c.get(), {}, ja, jb, nullptr);
+                  [d, u, tb, c, aln](FutRef *ia, FutRef *ib) {
+                      return issue_serial(d.get(), [d, u, tb, c, aln](FutRef *ja, FutRef *jb) {
+                          return heat2d_run_impl(d, u, tb, c.get(), {}, ja, jb, nullptr, aln);
                       }, nullptr, ia, ib);
                   },
                   &a, &b);
     } else {
         st = issue_serial(
             d.get(),
-            [d, u, tb, c, dv](FutRef *ia, FutRef *ib) {
-                return heat2d_run_impl(d, u, tb, c.get(), dv, ia, ib, nullptr);
+            [d, u, tb, c, dv, aln](FutRef *ia, FutRef *ib) {
+                return heat2d_run_impl(d, u, tb, c.get(), dv, ia, ib, nullptr, aln);
             },
             [&](FutRef *ia, FutRef *ib) {
-                return heat2d_run_impl(d, u, tb, c.get(), dv, ia, ib, stats_out);
+                return heat2d_run_impl(d, u, tb, c.get(), dv, ia, ib, stats_out, aln);
             },
             &a, &b);
         if (st) return st;
@@ -665,13 +664,24 @@ hxc_status hxc_heat2d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, const hxc
     return HXC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+hxc_status hxc_heat2d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, const hxc_heat2d_cfg *cfg,
+                          const hxc_future *deps, int ndeps, hxc_future *out,
+                          hxc_future *field_ready, hxc_run_stats *stats_out) {
+    hxc::drv::NvtxRange nvtx_range("hxc_heat2d_run");
+    return heat2d_run_entry(dh, uh, th, cfg, deps, ndeps, out, field_ready, stats_out, false);
+}
+
 }  // extern "C"
 
 namespace {
 
 hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const hxc_heat2d_cfg *cfg,
                            std::vector<FutRef> dv, FutRef *all_out, FutRef *field_out,
-                           hxc_run_stats *stats_out) {
+                           hxc_run_stats *stats_out, bool after_last_norms) {
     hxc_status st;
     if ((st = d->make_current())) return st;
 
@@ -724,10 +734,13 @@ hxc_status heat2d_run_impl(Ref<Device> d, Ref<Buffer> u, Ref<Buffer> tb, const h
             gs.next_rows = (nset + 1) % kGnormStages;
             norm_free = fut_order_only(gs.copied[nset]);
             gs.copied[nset] = FutRef();
-            // a run also starts after the last run's norm copy: measured, this
-            // keeps the host-memory runs issued back to back 2.5% faster (the
-            // resident loop loses 1%)
-            if (FutRef c = fut_order_only(gs.latest)) dv.push_back(c);
+            // a run from host memory also starts after the last run's norm
+            // copy (measured: host-memory runs issued back to back 2.5%
+            // faster).  Not a device-resident run: the norm copy queues
+            // behind the last snapshot's device->host copies, so the next
+            // run would wait for them (13 ms per 8192^2 pass measured)
+            if (after_last_norms)
+                if (FutRef c = fut_order_only(gs.latest)) dv.push_back(c);
         }
         if ((st = d->scratch_get("heat2d.norms." + std::to_string(nset), (size_t)n_snap * T * 8, &p)))
             return st;
@@ -1075,7 +1088,7 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dh, const double *host_u0, doubl
         inner.h2d_bytes += tl.tx(t) * tl.ty(t) * 8;
     }
     hxc_run_stats rs{};
-    if (!st) st = hxc_heat2d_run(dh, ub, tb, cfg, h2d.data(), (int)T, &run, &ready, &rs);
+    if (!st) st = heat2d_run_entry(dh, ub, tb, cfg, h2d.data(), (int)T, &run, &ready, &rs, true);
     for (int64_t t = 0; t < T && !st; t++) {
         size_t off = ((size_t)tl.y0(t) * nx + tl.x0(t)) * 8;
         hxc_future f = nullptr;

@@ -256,6 +256,42 @@ def test_heat2d_scaled_steps_large_magnitudes(dev):
         assert np.all(np.isfinite(got)) and relerr(got, want) <= TOL, mode
 
 
+def test_heat2d_kernel_launches_per_tile(dev):
+    """HXC_K_HEAT2D through hxc_launch, the canonical step
+    (t = fma(-4, u, s), u' = fma(r, t, u)): the tiles of a step launched on
+    their own stream slots, each after every tile of the step before (the
+    per-partition form of the paper's launch workflow); every tiling, odd
+    tile origins included, gives the same bits, within the tolerance of the
+    oracle."""
+    u0 = synth.bumps2d(150, 174, seed=237, nbumps=5, sigma=0.1)
+    ny, nx = u0.shape
+    steps, r = 9, 0.2
+
+    def run(tiles):
+        a, b = upload(dev, u0), dev.buffer(u0.nbytes)
+        rows = [p * ny // tiles[0] for p in range(tiles[0])] + [ny]
+        cols = [q * nx // tiles[1] for q in range(tiles[1])] + [nx]
+        prev = []
+        for s in range(steps):
+            src, dst = (a, b) if s % 2 == 0 else (b, a)
+            cur = []
+            for p in range(tiles[0]):
+                for q in range(tiles[1]):
+                    args = hxc.hxc_heat2d_args(src.h, dst.h, ny, nx, rows[p], cols[q],
+                                               rows[p + 1] - rows[p], cols[q + 1] - cols[q], r)
+                    cur.append(dev.launch(hxc.HXC_K_HEAT2D, args, slot=p * tiles[1] + q,
+                                          deps=prev))
+            prev = cur
+        assert hxc.wait_all(prev) == hxc.HXC_OK
+        return download(b if steps % 2 else a, (ny, nx))
+
+    ref = run((1, 1))
+    assert relerr(ref, oracle.heat2d(u0, r, steps)) <= TOL
+    for tiles in ((3, 4), (5, 2), (2, 7)):
+        got = run(tiles)
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), tiles
+
+
 def test_heat2d_rows_and_occupancy_knobs_bitexact(dev):
     """The strip height (rows per warp, including heights that are not
     multiples of the 32-row groups in which the strip-edge pair sums are
