@@ -502,8 +502,15 @@ def secondary(dev, timer, peaks):
                                                          deps=[d] if d else ())[0], reps=5, warm=2)
         res[mode] = {"ms": ms, "updates_per_s": n * st1 / (ms / 1e3)}
     speedups(res)
-    res["roofline"] = fp64_roof(3 * n * st1, res["graph"]["ms"], peaks,
-                                "3 FP64 operations per update, graph mode")
+    # FP64 operations per update by step kind (canonical, scaled, closing;
+    # hxc_heat1d_step_kinds): the sum ul + ur, then 2 FMAs, 1, or a product
+    # and an FMA
+    k1 = hxc.heat1d_step_kinds(0.25, st1)
+    ops1 = sum(c * o for c, o in zip(k1, (3, 2, 3)))
+    res["step_kinds"] = {"canonical": k1[0], "scaled": k1[1], "closing": k1[2]}
+    res["roofline"] = fp64_roof(ops1 * n, res["graph"]["ms"], peaks,
+                                "%.2f FP64 operations per update (%d scaled steps of 2, %d "
+                                "closing of 3), graph mode" % (ops1 / st1, k1[1], k1[2] + k1[0]))
     out["heat1d_2^20_8parts_100steps_f64"] = res
 
     # 3D periodic FP32 512^3, r = 0.15, 200 steps, 4 steps per launch

@@ -439,12 +439,24 @@ typedef struct {
  * its neighbours: in PLAIN and GRAPH mode step s of partition p runs after
  * step s-1 of p-1, p and p+1; FUSED mode advances `steps_per_launch` steps
  * per launch (0: the tuned count, knob heat1d.steps_per_launch, whose
- * default 0 puts all steps in one launch).  Results are bit-identical for
- * every partition count, mode and steps per launch. */
+ * default 0 puts all steps in one launch).  The steps' arithmetic is given
+ * under hxc_heat1d_step_kinds.  Results are bit-identical for every
+ * partition count, mode and steps per launch. */
 hxc_status hxc_heat1d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, int64_t n, int parts,
                           double r, int steps, hxc_mode mode, int steps_per_launch,
                           const hxc_future *deps, int ndeps, hxc_future *out,
                           hxc_run_stats *stats);
+
+/* Step kinds of a 1D run (hxc_heat1d_run), as for the 2D runs
+ * (hxc_heat2d_step_kinds) with s = ul + ur: counts[1] scaled steps,
+ * v' = fma((1-2r)/r, v, s), 2 FP64 operations per point; counts[2] closing
+ * steps, u' = fma(r^(m+1), s, ((1-2r) r^m) v), 3 operations; counts[0]
+ * canonical steps, t = fma(-2, u, s), u' = fma(r, t, u), 3 operations (every
+ * step when r is outside (0, 1/2] or r^-1 > 2^48).  The intervals are of
+ * min(steps, 128) steps (what one captured graph holds), cut into groups of
+ * at most M + 1 steps, M the largest m with r^-m <= 2^48 (24 at r = 1/4).
+ * counts: 3 int64 written.  Host only, no device needed. */
+hxc_status hxc_heat1d_step_kinds(double r, int steps, int64_t *counts);
 
 typedef struct {
     int64_t ny, nx;            /* field shape */

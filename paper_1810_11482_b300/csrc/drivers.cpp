@@ -16,7 +16,7 @@
 #include <memory>
 
 #include "drivers_util.hpp"
-#include "ftcs2_plan.hpp"
+#include "ftcs_plan.hpp"
 #include "kernels.cuh"
 #include "tune.hpp"
 #include "runtime.hpp"
@@ -40,6 +40,7 @@ struct Heat1dPlan {
     int64_t n;
     std::vector<int64_t> b;
     double r;
+    std::shared_ptr<const k::FtcsPlan> plan;  // the run's step kinds (ftcs_plan)
 };
 
 // Partitions whose cells fall in the periodic window [lo - T, hi + T).
@@ -63,12 +64,12 @@ std::vector<int> halo_parts(const std::vector<int64_t> &b, int64_t n, int p, int
     return out;
 }
 
-// Issues `steps` 1D steps, `T` steps per launch, partition p on slot p.
-// prev[p] holds the last future of partition p and is updated.  `flip` is
-// the index of the buffer holding the current state; every launch moves the
-// state to the other buffer.
+// Issues `steps` 1D steps (run steps g0 .. g0+steps-1), `T` steps per
+// launch, partition p on slot p.  prev[p] holds the last future of
+// partition p and is updated.  `flip` is the index of the buffer holding
+// the current state; every launch moves the state to the other buffer.
 hxc_status issue_heat1d(const Heat1dPlan &pl, int steps, int T, int &flip, std::vector<FutRef> &prev,
-                        Stats &stats) {
+                        Stats &stats, int64_t g0) {
     int parts = (int)pl.b.size() - 1;
     std::vector<std::vector<int>> nb(parts);
     for (int p = 0; p < parts; p++) nb[p] = halo_parts(pl.b, pl.n, p, T);
@@ -86,7 +87,8 @@ hxc_status issue_heat1d(const Heat1dPlan &pl, int steps, int T, int &flip, std::
                 if (prev[q]) deps.push_back(prev[q]);
             int64_t lo = pl.b[p], cnt = pl.b[p + 1] - pl.b[p];
             int64_t n = pl.n;
-            double r = pl.r;
+            std::shared_ptr<const k::FtcsPlan> plan = pl.plan;
+            const int64_t gs = g0 + done;
             hxc_launch_cfg cfg{};
             const hxc_launch_cfg *pc = nullptr;
             if (t > 1) {
@@ -97,7 +99,7 @@ hxc_status issue_heat1d(const Heat1dPlan &pl, int steps, int T, int &flip, std::
                 pc = &cfg;
             }
             StreamOp op = [=](cudaStream_t s) {
-                return k::heat1d(src, dst, n, lo, cnt, r, t, pc ? &cfg : nullptr, s);
+                return k::heat1d_plan(src, dst, n, lo, cnt, *plan, gs, t, pc ? &cfg : nullptr, s);
             };
             hxc_status st = issue_device_op(pl.dev, p, deps, op, {}, &cur[p]);
             if (st) return st;
@@ -154,7 +156,8 @@ hxc_status hxc_heat1d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
     }
     Stats stats{stats_out};
     if ((st = d->make_current())) return st;
-    Heat1dPlan pl{d.get(), {(double *)u->ptr, (double *)t->ptr}, n, split(n, parts, false), r};
+    Heat1dPlan pl{d.get(), {(double *)u->ptr, (double *)t->ptr}, n, split(n, parts, false), r,
+                  std::make_shared<const k::FtcsPlan>(ftcs_plan(1, r, steps, heat1d_interval(steps)))};
     int T = 1;
     if (mode == HXC_MODE_FUSED) {
         if (steps_per_launch == 0) {
@@ -175,10 +178,10 @@ hxc_status hxc_heat1d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
         for (auto &p : prev) p = j;
     }
     if (mode == HXC_MODE_GRAPH && steps > 0) {
-        // capture `chunk` steps once (an even count when replayed more than
-        // once, so every replay starts from u) and replay it; the remaining
-        // steps are issued directly
-        int chunk = steps <= 128 ? steps : 128;
+        // capture `chunk` steps (one interval of the step kinds) once (an
+        // even count when replayed more than once, so every replay starts
+        // from u) and replay it; the remaining steps are issued directly
+        int chunk = (int)heat1d_interval(steps);
         int reps = steps / chunk;
         std::string key = key_of("heat1d", {(double)n, (double)parts, r, (double)chunk},
                                  {u->ptr, t->ptr});
@@ -193,7 +196,7 @@ hxc_status hxc_heat1d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
             std::vector<FutRef> cprev(parts);
             Stats none{nullptr};
             int cflip = 0;
-            st = issue_heat1d(pl, chunk, 1, cflip, cprev, none);
+            st = issue_heat1d(pl, chunk, 1, cflip, cprev, none, 0);
             Ref<Graph> ng;
             hxc_status st2 = graph_end(d.get(), &ng);
             if (st) return st;
@@ -221,9 +224,10 @@ hxc_status hxc_heat1d_run(hxc_device dh, hxc_buffer uh, hxc_buffer th, int64_t n
         }
         flip = (reps * chunk) % 2;
         int rest = steps - reps * chunk;
-        if (rest > 0 && (st = issue_heat1d(pl, rest, 1, flip, prev, stats))) return st;
+        if (rest > 0 && (st = issue_heat1d(pl, rest, 1, flip, prev, stats, (int64_t)reps * chunk)))
+            return st;
     } else if (steps > 0) {
-        if ((st = issue_heat1d(pl, steps, T, flip, prev, stats))) return st;
+        if ((st = issue_heat1d(pl, steps, T, flip, prev, stats, 0))) return st;
     }
     // the result lands in buf[flip]; bring it back into u
     if (flip == 1) {
@@ -333,7 +337,7 @@ struct Heat2dRun {
 };
 
 // Issues steps [s0, s1), one interval of the run (its step kinds follow
-// ftcs2_step), per tile or fused.
+// ftcs_step), per tile or fused.
 hxc_status issue_steps2d(Heat2dRun &R, int64_t s0, int64_t s1, std::vector<FutRef> &prev,
                          bool fused) {
     const hxc_heat2d_cfg &c = *R.cfg;
@@ -341,7 +345,7 @@ hxc_status issue_steps2d(Heat2dRun &R, int64_t s0, int64_t s1, std::vector<FutRe
     for (int64_t s = s0; s < s1; s++) {
         const double *src = R.buf[s % 2];
         double *dst = R.buf[(s + 1) % 2];
-        const k::Ftcs2Step kind = ftcs2_step(c.r, s - s0, s1 - s0);
+        const k::FtcsStep kind = ftcs2_step(c.r, s - s0, s1 - s0);
         if (fused) {
             std::vector<FutRef> deps;
             for (auto &f : prev)
@@ -1147,12 +1151,21 @@ hxc_status hxc_heat2d_run_host(hxc_device dh, const double *host_u0, double *hos
 }
 
 
+hxc_status hxc_heat1d_step_kinds(double r, int steps, int64_t *counts) {
+    if (!counts || steps < 0) {
+        set_error("hxc_heat1d_step_kinds: invalid arguments");
+        return HXC_E_INVALID;
+    }
+    ftcs_count(1, r, steps, heat1d_interval(steps), counts);
+    return HXC_OK;
+}
+
 hxc_status hxc_heat2d_step_kinds(const hxc_heat2d_cfg *cfg, int64_t *counts) {
     if (!cfg || !counts || cfg->steps < 0 || cfg->snapshot_every < 0) {
         set_error("hxc_heat2d_step_kinds: invalid arguments");
         return HXC_E_INVALID;
     }
-    ftcs2_count(cfg->r, cfg->steps, heat2d_interval(*cfg), counts);
+    ftcs_count(2, cfg->r, cfg->steps, heat2d_interval(*cfg), counts);
     return HXC_OK;
 }
 

@@ -20,7 +20,7 @@
 #include <vector>
 
 #include "drivers_util.hpp"
-#include "ftcs2_plan.hpp"
+#include "ftcs_plan.hpp"
 #include "kernels.cuh"
 #include "runtime.hpp"
 
@@ -40,7 +40,7 @@ struct StreamPlan {
 
 // Copy in, step, copy out of tile t from src to dst (host arrays).
 cudaError_t tile_step(const StreamPlan &pl, int64_t t, const double *src, double *dst,
-                      const k::Ftcs2Step &kind, cudaStream_t s) {
+                      const k::FtcsStep &kind, cudaStream_t s) {
     const int64_t p = t / pl.TX, q = t % pl.TX;
     const int64_t y0 = pl.by[p], y1 = pl.by[p + 1], x0 = pl.bx[q], x1 = pl.bx[q + 1];
     const int64_t r0 = std::max<int64_t>(y0 - 1, 0), r1 = std::min<int64_t>(y1 + 1, pl.ny);
@@ -123,7 +123,7 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
         for (int step = 0; step < steps && e == cudaSuccess; step++) {
             const double *src = step % 2 ? host_b : host_a;
             double *dst = step % 2 ? host_a : host_b;
-            const k::Ftcs2Step kind = step_kind(step);
+            const k::FtcsStep kind = step_kind(step);
             for (int64_t t = 0; t < T && e == cudaSuccess; t++) {
                 e = tile_step(pl, t, src, dst, kind, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -147,7 +147,7 @@ extern "C" hxc_status hxc_heat2d_stream_run(hxc_device dh, double *host_a, doubl
     for (int step = 0; step < steps; step++) {
         const double *src = step % 2 ? host_b : host_a;
         double *dst = step % 2 ? host_a : host_b;
-        const k::Ftcs2Step kind = step_kind(step);
+        const k::FtcsStep kind = step_kind(step);
         for (int64_t t = 0; t < T; t++) {
             std::vector<FutRef> deps_t;
             if (step == 0) {

@@ -64,10 +64,30 @@ __device__ __forceinline__ double addf(double a, double b, double one) {
     return __fma_rn(a, one, b);
 }
 
-__device__ __forceinline__ double ftcs3(double ul, double u, double ur, double r, double one) {
-    double s = addf(ul, ur, one);
-    double t = __fma_rn(-2.0, u, s);
-    return __fma_rn(r, t, u);
+// The 1D update of kind M (kFtcsCanon / Scaled / Close, kernels.cuh).
+template <int M>
+__device__ __forceinline__ double ftcs3(double ul, double u, double ur, double c0, double c1,
+                                        double one) {
+    const double s = addf(ul, ur, one);
+    if constexpr (M == kFtcsScaled) {
+        return __fma_rn(c0, u, s);
+    } else if constexpr (M == kFtcsClose) {
+        return __fma_rn(c0, s, __dmul_rn(c1, u));
+    } else {
+        const double t = __fma_rn(-2.0, u, s);
+        return __fma_rn(c0, t, u);
+    }
+}
+
+// Kind and coefficients of run step g under `p` (the rule of ftcs_step,
+// evaluated from the plan's table, on either side).
+__host__ __device__ __forceinline__ FtcsStep plan_step(const FtcsPlan &p, int64_t g) {
+    if (p.P == 0) return {kFtcsCanon, p.r, 0.0};
+    const int64_t j = g % p.I, s0 = g - j;
+    const int64_t L = p.total - s0 < p.I ? p.total - s0 : (int64_t)p.I;
+    const int64_t q = j % p.P, end = L < j - q + p.P ? L : j - q + p.P;
+    if (j + 1 < end) return {kFtcsScaled, p.k, 0.0};
+    return {kFtcsClose, p.a[q], p.b[q]};
 }
 
 // One 2D pair sum (uE + uS of a point, = uN + uW of the point below and to
@@ -80,16 +100,16 @@ __device__ __forceinline__ double pair2(double a, double b, double one) {
 // The 2D update from the point's two pair sums, pNW = uN + uW and
 // pSE = uE + uS; their sum on the integer-pipe adder when E >= 2.  Every E
 // gives the same bits; the split balances the FP64 pipe against the
-// integer pipe.  M is the step kind (kFtcs2Canon / Scaled / Close): the
+// integer pipe.  M is the step kind (kFtcsCanon / Scaled / Close): the
 // scaled step is one FMA after the sum, so a scaled run costs 3 FP64
 // operations per point instead of 4.
 template <int E, int M>
 __device__ __forceinline__ double ftcs5p(double u, double pNW, double pSE, double c0, double c1,
                                          double one) {
     const double s = E >= 2 ? dadd_int(pNW, pSE) : addf(pNW, pSE, one);
-    if constexpr (M == kFtcs2Scaled) {
+    if constexpr (M == kFtcsScaled) {
         return __fma_rn(c0, u, s);
-    } else if constexpr (M == kFtcs2Close) {
+    } else if constexpr (M == kFtcsClose) {
         return __fma_rn(c0, s, __dmul_rn(c1, u));
     } else {
         const double t = __fma_rn(-4.0, u, s);
@@ -150,13 +170,15 @@ cudaError_t partition(double *x, int64_t n, const hxc_launch_cfg *cfg, cudaStrea
 }
 
 // ------------------------------------------------------------ 1D FTCS
+template <int M>
 __global__ void k_heat1d_step(const double *__restrict__ src, double *__restrict__ dst,
-                              int64_t n, int64_t lo, int64_t count, double r, double one) {
+                              int64_t n, int64_t lo, int64_t count, double c0, double c1,
+                              double one) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t j = lo + t;
         int64_t jl = j == 0 ? n - 1 : j - 1, jr = j == n - 1 ? 0 : j + 1;
-        dst[j] = ftcs3(src[jl], src[j], src[jr], r, one);
+        dst[j] = ftcs3<M>(src[jl], src[j], src[jr], c0, c1, one);
     }
 }
 
@@ -165,7 +187,8 @@ __global__ void k_heat1d_step(const double *__restrict__ src, double *__restrict
 // T steps there (the valid window shrinks by one point per side per step)
 // and writes its C points.  Chunks are visited grid-stride.
 __global__ void k_heat1d_tb(const double *__restrict__ src, double *__restrict__ dst, int64_t n,
-                            int64_t lo, int64_t count, double r, int T, int C, double one) {
+                            int64_t lo, int64_t count, const __grid_constant__ FtcsPlan plan,
+                            int64_t g0, int T, int C, double one) {
     extern __shared__ double sm[];
     const int W = C + 2 * T;
     double *a = sm, *b = sm + W;
@@ -183,8 +206,17 @@ __global__ void k_heat1d_tb(const double *__restrict__ src, double *__restrict__
         __syncthreads();
         double *pa = a, *pb = b;
         for (int s = 1; s <= T; s++) {
-            for (int i = s + threadIdx.x; i < W - s; i += blockDim.x)
-                pb[i] = ftcs3(pa[i - 1], pa[i], pa[i + 1], r, one);
+            const FtcsStep st = plan_step(plan, g0 + s - 1);  // uniform per level
+            if (st.kind == kFtcsScaled) {
+                for (int i = s + threadIdx.x; i < W - s; i += blockDim.x)
+                    pb[i] = ftcs3<kFtcsScaled>(pa[i - 1], pa[i], pa[i + 1], st.c0, st.c1, one);
+            } else if (st.kind == kFtcsClose) {
+                for (int i = s + threadIdx.x; i < W - s; i += blockDim.x)
+                    pb[i] = ftcs3<kFtcsClose>(pa[i - 1], pa[i], pa[i + 1], st.c0, st.c1, one);
+            } else {
+                for (int i = s + threadIdx.x; i < W - s; i += blockDim.x)
+                    pb[i] = ftcs3<kFtcsCanon>(pa[i - 1], pa[i], pa[i + 1], st.c0, st.c1, one);
+            }
             __syncthreads();
             double *t = pa;
             pa = pb;
@@ -196,13 +228,24 @@ __global__ void k_heat1d_tb(const double *__restrict__ src, double *__restrict__
     }
 }
 
-cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
-                   double r, int steps, const hxc_launch_cfg *cfg, cudaStream_t s) {
+cudaError_t heat1d_plan(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
+                        const FtcsPlan &plan, int64_t g0, int steps, const hxc_launch_cfg *cfg,
+                        cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     if (steps == 1) {
         unsigned b = block_from(cfg, 256);
         unsigned g = grid_from(cfg, std::min<int64_t>((count + b - 1) / b, sm_count() * 8));
-        k_heat1d_step<<<g, b, 0, s>>>(src, dst, n, lo, count, r, 1.0);
+        const FtcsStep st = plan_step(plan, g0);  // decided on the host
+        switch (st.kind) {
+            case kFtcsScaled:
+                k_heat1d_step<kFtcsScaled><<<g, b, 0, s>>>(src, dst, n, lo, count, st.c0, st.c1, 1.0);
+                break;
+            case kFtcsClose:
+                k_heat1d_step<kFtcsClose><<<g, b, 0, s>>>(src, dst, n, lo, count, st.c0, st.c1, 1.0);
+                break;
+            default:
+                k_heat1d_step<kFtcsCanon><<<g, b, 0, s>>>(src, dst, n, lo, count, st.c0, st.c1, 1.0);
+        }
         return cudaGetLastError();
     }
     unsigned b = block_from(cfg, 512);
@@ -217,8 +260,18 @@ cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_
     static std::atomic<uint64_t> attr{0};
     cudaError_t e = smem_optin(k_heat1d_tb, 227 * 1024, attr);
     if (e != cudaSuccess) return e;
-    k_heat1d_tb<<<g, b, smem, s>>>(src, dst, n, lo, count, r, steps, (int)C, 1.0);
+    k_heat1d_tb<<<g, b, smem, s>>>(src, dst, n, lo, count, plan, g0, steps, (int)C, 1.0);
     return cudaGetLastError();
+}
+
+cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
+                   double r, int steps, const hxc_launch_cfg *cfg, cudaStream_t s) {
+    FtcsPlan p{};
+    p.r = r;
+    p.P = 0;
+    p.I = 1;
+    p.total = steps;
+    return heat1d_plan(src, dst, n, lo, count, p, 0, steps, cfg, s);
 }
 
 // ------------------------------------------------------------ 2D FTCS
@@ -399,22 +452,22 @@ cudaError_t heat2d_launch(const double *src, double *dst, int64_t ny, int64_t nx
 cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
                    const hxc_launch_cfg *cfg, cudaStream_t s) {
-    return heat2d_launch<kFtcs2Canon>(src, dst, ny, nx, y0, x0, ty, tx, r, 0.0, rows_per_warp,
+    return heat2d_launch<kFtcsCanon>(src, dst, ny, nx, y0, x0, ty, tx, r, 0.0, rows_per_warp,
                                       cfg, s);
 }
 
 cudaError_t heat2d_step(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
-                        int64_t x0, int64_t ty, int64_t tx, const Ftcs2Step &step,
+                        int64_t x0, int64_t ty, int64_t tx, const FtcsStep &step,
                         int rows_per_warp, cudaStream_t s) {
     switch (step.kind) {
-        case kFtcs2Scaled:
-            return heat2d_launch<kFtcs2Scaled>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
+        case kFtcsScaled:
+            return heat2d_launch<kFtcsScaled>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
                                                rows_per_warp, nullptr, s);
-        case kFtcs2Close:
-            return heat2d_launch<kFtcs2Close>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
+        case kFtcsClose:
+            return heat2d_launch<kFtcsClose>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
                                               rows_per_warp, nullptr, s);
         default:
-            return heat2d_launch<kFtcs2Canon>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
+            return heat2d_launch<kFtcsCanon>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
                                               rows_per_warp, nullptr, s);
     }
 }

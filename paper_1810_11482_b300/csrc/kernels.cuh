@@ -47,9 +47,41 @@ cudaError_t mandelbrot(uint8_t *rgb, int32_t *counts, int64_t width, int64_t hei
                        float y0, float dx, float dy, int32_t max_iter, const hxc_launch_cfg *cfg,
                        cudaStream_t s);
 
-// dst[lo, lo+count) <- `steps` periodic FTCS steps of src (period n).
+// Kinds of FTCS step in d dimensions (d = 1, 2).  With s the sum of the 2d
+// neighbours of the values read ((uN + uW) + (uE + uS) in 2D, ul + ur in 1D):
+//   kFtcsCanon  (c0 = r):             t = fma(-2d, u, s); u' = fma(r, t, u)
+//   kFtcsScaled (c0 = (1 - 2d r)/r):  u' = fma(c0, u, s)
+//   kFtcsClose  (c0, c1):             u' = fma(c0, s, c1 * u)
+// A scaled step maps v = u_n / r^m to u_{n+1} / r^(m+1); a closing step
+// with c0 = r^(m+1), c1 = (1 - 2d r) r^m maps v = u_n / r^m to u_{n+1}.
+enum : int { kFtcsCanon = 0, kFtcsScaled = 1, kFtcsClose = 2 };
+struct FtcsStep {
+    int kind;
+    double c0, c1;
+};
+
+// The step kinds of a whole run, for kernels that advance several steps per
+// launch.  Run step g (0-based, of `total`) is step j = g mod I of its
+// interval (I steps, the last interval shorter); an interval is cut into
+// groups of P steps (the last shorter) whose last step closes; the others
+// are scaled.  P = 0: every step canonical with r.  The closing step after q
+// scaled steps uses a[q], b[q].
+constexpr int kFtcsMaxGroup = 65;
+struct FtcsPlan {
+    double r, k;
+    int P, I;
+    int64_t total;
+    double a[kFtcsMaxGroup], b[kFtcsMaxGroup];
+};
+
+// dst[lo, lo+count) <- `steps` periodic FTCS steps of src (period n),
+// canonical arithmetic.
 cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
                    double r, int steps, const hxc_launch_cfg *cfg, cudaStream_t s);
+// The same, run steps g0 .. g0+steps-1 of a run whose kinds `plan` gives.
+cudaError_t heat1d_plan(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
+                        const FtcsPlan &plan, int64_t g0, int steps, const hxc_launch_cfg *cfg,
+                        cudaStream_t s);
 // Largest `steps` a single temporally blocked 1D launch accepts.
 constexpr int kHeat1dMaxSteps = 1024;
 
@@ -58,20 +90,8 @@ constexpr int kHeat1dMaxSteps = 1024;
 cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
                    const hxc_launch_cfg *cfg, cudaStream_t s);
-
-// Kinds of 2D step.  With s = (uN + uW) + (uE + uS) of the values read:
-//   kFtcs2Canon  (c0 = r):           t = fma(-4, u, s); u' = fma(r, t, u)
-//   kFtcs2Scaled (c0 = (1 - 4r)/r):  u' = fma(c0, u, s)
-//   kFtcs2Close  (c0, c1):           u' = fma(c0, s, c1 * u)
-// A scaled step maps v = u_n / r^m to u_{n+1} / r^(m+1); a closing step
-// with c0 = r^(m+1), c1 = (1 - 4r) r^m maps v = u_n / r^m to u_{n+1}.
-enum : int { kFtcs2Canon = 0, kFtcs2Scaled = 1, kFtcs2Close = 2 };
-struct Ftcs2Step {
-    int kind;
-    double c0, c1;
-};
 cudaError_t heat2d_step(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
-                        int64_t x0, int64_t ty, int64_t tx, const Ftcs2Step &step,
+                        int64_t x0, int64_t ty, int64_t tx, const FtcsStep &step,
                         int rows_per_warp, cudaStream_t s);
 
 // 2D kernel knobs (tuning registry): share of the additions run on the

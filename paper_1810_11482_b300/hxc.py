@@ -227,6 +227,7 @@ _SIGS = {
                                         ctypes.POINTER(c_fut), ctypes.c_int, ctypes.POINTER(c_fut),
                                         ctypes.POINTER(hxc_run_stats)]),
     "hxc_heat2d_step_kinds": (c_st, [ctypes.c_void_p, ctypes.POINTER(i64)]),
+    "hxc_heat1d_step_kinds": (c_st, [ctypes.c_double, ctypes.c_int, ctypes.POINTER(i64)]),
     "hxc_host_norms": (c_st, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(i64), ctypes.c_int,
                               ctypes.c_void_p]),
     "hxc_heat2d_stream_run": (c_st, [c_dev, ctypes.c_void_p, ctypes.c_void_p, i64, i64, i64, i64,
@@ -716,6 +717,13 @@ def _f64_host(a, what):
     if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
         raise ValueError(what + " must be a C-contiguous float64 array")
     return a.ctypes.data
+
+
+def heat1d_step_kinds(r, steps):
+    """(canonical, scaled, closing) step counts of a 1D run."""
+    out = (i64 * 3)()
+    check(lib().hxc_heat1d_step_kinds(r, steps, out), "heat1d_step_kinds")
+    return tuple(int(v) for v in out)
 
 
 def heat2d_step_kinds(cfg):

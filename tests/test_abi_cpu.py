@@ -329,3 +329,27 @@ def test_heat2d_step_kinds_arguments(L):
     cfg = hxc.heat2d_cfg(64, 64, 1, 1, 0.2, -1, 0, "fused", None, None)
     assert L.hxc_heat2d_step_kinds(ctypes.byref(cfg), (ctypes.c_int64 * 3)()) == hxc.HXC_E_INVALID
     assert L.hxc_heat2d_step_kinds(None, (ctypes.c_int64 * 3)()) == hxc.HXC_E_INVALID
+
+
+@pytest.mark.parametrize("r,steps,want", [
+    # r = 1/4: (1/4)^24 = 2^-48, so 24 scaled steps in a row; an interval of
+    # 100 steps is 4 groups of 25
+    (0.25, 100, (0, 96, 4)),
+    # 300 steps: intervals of 128, 128, 44; 6 + 6 + 2 groups
+    (0.25, 300, (0, 286, 14)),
+    (0.25, 1, (0, 0, 1)),
+    # r = 1/2: (1 - 2r)/r = 0, 48 scaled steps in a row: 100 = 49 + 49 + 2
+    (0.5, 100, (0, 97, 3)),
+    (0.6, 10, (10, 0, 0)),     # beyond the stability bound: canonical
+    (1e-17, 10, (10, 0, 0)),   # one scaled step would grow 1e17 > 2^48
+    (0.25, 0, (0, 0, 0)),
+])
+def test_heat1d_step_kinds(L, r, steps, want):
+    """The 1D runs' schedule of scaled and closing steps (host only)."""
+    assert hxc.heat1d_step_kinds(r, steps) == want
+    assert sum(want) == steps
+
+
+def test_heat1d_step_kinds_arguments(L):
+    assert L.hxc_heat1d_step_kinds(0.25, -1, (ctypes.c_int64 * 3)()) == hxc.HXC_E_INVALID
+    assert L.hxc_heat1d_step_kinds(0.25, 5, None) == hxc.HXC_E_INVALID

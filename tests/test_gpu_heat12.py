@@ -131,6 +131,37 @@ def test_heat1d_translation_and_reflection_exact(dev):
     assert np.array_equal(got, ref[::-1])
 
 
+@pytest.mark.parametrize("r", [0.25, 0.5, 0.2, 0.01, 1e-17])
+def test_heat1d_scaled_steps_vs_oracle(dev, r):
+    """The 1D runs' scaled and closing steps (hxc_heat1d_step_kinds): 300
+    steps are three intervals (128, 128, 44), so graph mode replays its
+    graph twice and issues the rest; fused launches of 300, 50 and 7 steps
+    straddle the intervals and groups.  Every mode, partition count and
+    steps per launch gives the same bits, within the FP64 tolerance of the
+    oracle; r = 1e-17 runs canonical steps only."""
+    n, steps = 3001, 300
+    u0 = synth.heat1d_input(n, seed=104)
+    kinds = hxc.heat1d_step_kinds(r, steps)
+    assert sum(kinds) == steps and (kinds[0] == steps) == (r == 1e-17)
+    ref, _ = run1d(dev, u0, 1, r, steps, "plain")
+    assert relerr(ref, oracle.heat1d(u0, r, steps)) <= TOL
+    for parts in (1, 3, 8):
+        for mode, spl in (("plain", 0), ("graph", 0), ("fused", 0), ("fused", 50), ("fused", 7)):
+            got, _ = run1d(dev, u0, parts, r, steps, mode, spl)
+            assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), (parts, mode, spl)
+
+
+def test_heat1d_scaled_steps_large_magnitudes(dev):
+    """A field of magnitude 2^900 at r = 1/4 (the scaled field grows by up
+    to 4^24 = 2^48 before each closing step): finite, within the tolerance
+    of the oracle."""
+    u0 = synth.heat1d_input(2048, seed=105) * 2.0 ** 900
+    want = oracle.heat1d(u0, 0.25, 120)
+    for mode in ("plain", "fused"):
+        got, _ = run1d(dev, u0, 4, 0.25, 120, mode)
+        assert np.all(np.isfinite(got)) and relerr(got, want) <= TOL, mode
+
+
 def test_heat1d_full_config_vs_oracle(dev):
     """2^20 points, 8 partitions, r = 1/4, 100 steps, every mode."""
     n, r, steps = 1 << 20, 0.25, 100
