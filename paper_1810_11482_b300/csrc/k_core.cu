@@ -14,12 +14,13 @@
 // sums are symmetric under transposition and under a half turn, so
 // transposed or reversed inputs give transposed or reversed bits.
 //
-// The 2D runs use two more step kinds of the same sums (kernels.cuh): FTCS
-// is linear, so u_{n+1} = r ((1 - 4r)/r u_n + s(u_n)), and the field scaled
-// by r^-m after m steps advances by one FMA after the sum (3 operations per
-// point); a closing step takes the scaled field back to true values.  Which
-// step of a run is which kind depends only on the step's index, so the bit-
-// identity across partitions, schedules and graph replay holds for them too.
+// The 1D and 2D runs use two more step kinds of the same sums (kernels.cuh):
+// FTCS is linear, so u_{n+1} = r ((1 - 2d r)/r u_n + s(u_n)) in d dimensions,
+// and the field scaled by r^-m after m steps advances by one FMA after the
+// sum (2 operations per point in 1D, 3 in 2D); a closing step takes the
+// scaled field back to true values.  Which step of a run is which kind
+// depends only on the step's index, so the bit-identity across partitions,
+// schedules, steps per launch and graph replay holds for them too.
 #include "fp64_int.cuh"
 #include "kernels.cuh"
 #include "tune.hpp"
