@@ -1,5 +1,6 @@
 """Small, self-contained cases for profiling one kernel at a time.
 
+    python -m paper_1810_11482_b300.profile_cases heat1d [log2 n] [parts] [steps] [fused 0/1]
     python -m paper_1810_11482_b300.profile_cases heat2d [n] [launches]
     python -m paper_1810_11482_b300.profile_cases heat3d [nz ny nx] [steps]
     python -m paper_1810_11482_b300.profile_cases heat3d_step [nz ny nx] [steps]
@@ -17,6 +18,17 @@ import sys
 import numpy as np
 
 from . import hxc, synth
+
+
+def heat1d(log2n=20, parts=8, steps=100, fused=0):
+    dev = hxc.get_all_devices(2, 0)[0]
+    n = 1 << log2n
+    u0 = synth.heat1d_input(n, seed=1)
+    u, t = dev.buffer(u0.nbytes), dev.buffer(u0.nbytes)
+    u.write(u0).get()
+    f, st = hxc.heat1d_run(dev, u, t, n, parts, 0.25, steps, "fused" if fused else "plain", 0)
+    f.get()
+    return st.kernel_launches
 
 
 def heat2d(n=4096, launches=3):
@@ -93,7 +105,7 @@ def mandelbrot(side=4096, max_iter=256):
     return 1
 
 
-CASES = {"heat2d": heat2d, "heat3d": heat3d, "heat3d_step": heat3d_step, "batch": batch,
+CASES = {"heat1d": heat1d, "heat2d": heat2d, "heat3d": heat3d, "heat3d_step": heat3d_step, "batch": batch,
          "adjoint": adjoint,
          "partition": partition, "mandelbrot": mandelbrot}
 
