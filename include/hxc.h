@@ -509,7 +509,11 @@ hxc_status hxc_heat2d_run_host(hxc_device dev, const double *host_u0, double *ho
  * largest field used; a pair outgrown by a larger call stays allocated (an
  * operation still to be issued may hold it) until the process ends.
  * A call's steps also start after the device-norm copy of the 2D run
- * issued before it (measured: back-to-back calls 2.5% faster).
+ * issued before it (measured: back-to-back calls 6% faster).  A call that
+ * has to wait for unfinished host work (a dependency that is a promise or a
+ * host continuation, or the call that used its field pair last) is issued
+ * as a whole by the worker pool once every dependency is done; its stats
+ * then count nothing.
  * Argument errors are returned synchronously with no future created; a
  * failure of a copy or of the run is stored in *out and does not affect
  * later calls. */

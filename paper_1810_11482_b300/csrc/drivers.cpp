@@ -668,6 +668,97 @@ hxc_status heat2d_run_entry(hxc_device dh, hxc_buffer uh, hxc_buffer th, const h
     return HXC_OK;
 }
 
+// Issues one call of hxc_heat2d_run_host_async into device field pair
+// `slot` after `deps`: the tile uploads, the run and the tile downloads.
+// *all receives the future of the whole call; after a failure, the future
+// of whatever was issued (or none).
+hxc_status host_run_issue(hxc_device dh, Device *d, int slot, const double *host_u0,
+                          double *host_uT, const hxc_heat2d_cfg *cfg,
+                          const std::vector<FutRef> &deps, FutRef *all_out,
+                          hxc_run_stats *stats_out) {
+    const size_t field = (size_t)cfg->ny * cfg->nx * 8;
+    hxc_status st;
+    void *pu, *pt;
+    if ((st = d->scratch_get(kHostKeyU[slot], field, &pu))) return st;
+    if ((st = d->scratch_get(kHostKeyT[slot], field, &pt))) return st;
+    hxc_buffer ub, tb;
+    hxc_buffer_wrap(dh, pu, field, &ub);
+    hxc_buffer_wrap(dh, pt, field, &tb);
+    Tiles tl;
+    tl.TY = cfg->tiles_y;
+    tl.TX = cfg->tiles_x;
+    tl.by = split(cfg->ny, cfg->tiles_y, false);
+    tl.bx = split(cfg->nx, cfg->tiles_x, true);
+    const int64_t T = tl.count(), nx = cfg->nx;
+    hxc_run_stats inner{};
+    std::vector<hxc_future> in_deps;
+    for (auto &f : deps) in_deps.push_back(to_handle(f));
+    std::vector<hxc_future> h2d, d2h;
+    hxc_future run = nullptr, ready = nullptr;
+    auto cleanup = [&]() {
+        for (auto f : in_deps) hxc_future_release(f);
+        for (auto f : h2d) hxc_future_release(f);
+        for (auto f : d2h) hxc_future_release(f);
+        if (run) hxc_future_release(run);
+        if (ready) hxc_future_release(ready);
+        hxc_buffer_release(ub);
+        hxc_buffer_release(tb);
+    };
+    // uploads and downloads on their own stream slots, so that they overlap
+    // the steps of the call issued before this one
+    for (int64_t t = 0; t < T && !st; t++) {
+        size_t off = ((size_t)tl.y0(t) * nx + tl.x0(t)) * 8;
+        hxc_future f = nullptr;
+        st = hxc_buffer_enqueue_write_2d(ub, off, nx * 8, (const char *)host_u0 + off, nx * 8,
+                                         tl.tx(t) * 8, tl.ty(t), kHostInSlot0 + (int)(t % kHostSlots),
+                                         in_deps.data(), (int)in_deps.size(), &f);
+        if (!st) h2d.push_back(f);
+        inner.copies++;
+        inner.h2d_bytes += tl.tx(t) * tl.ty(t) * 8;
+    }
+    hxc_run_stats rs{};
+    if (!st) st = heat2d_run_entry(dh, ub, tb, cfg, h2d.data(), (int)T, &run, &ready, &rs, true);
+    for (int64_t t = 0; t < T && !st; t++) {
+        size_t off = ((size_t)tl.y0(t) * nx + tl.x0(t)) * 8;
+        hxc_future f = nullptr;
+        st = hxc_buffer_enqueue_read_2d(ub, off, nx * 8, (char *)host_uT + off, nx * 8,
+                                        tl.tx(t) * 8, tl.ty(t), kHostOutSlot0 + (int)(t % kHostSlots),
+                                        &ready, 1, &f);
+        if (!st) d2h.push_back(f);
+        inner.copies++;
+        inner.d2h_bytes += tl.tx(t) * tl.ty(t) * 8;
+    }
+    hxc_future all = nullptr;
+    if (!st) {
+        d2h.push_back(run);
+        run = nullptr;
+        st = hxc_when_all(d2h.data(), (int)d2h.size(), &all);
+    }
+    if (st) {
+        // nothing more is issued into this pair; its next user waits for
+        // whatever did get issued
+        std::vector<hxc_future> issued(h2d);
+        issued.insert(issued.end(), d2h.begin(), d2h.end());
+        if (run) issued.push_back(run);
+        hxc_future j = nullptr;
+        if (!issued.empty() && hxc_when_all(issued.data(), (int)issued.size(), &j) == HXC_OK) {
+            *all_out = fut_order_only(fut_from_handle(j));
+            hxc_future_release(j);
+        }
+        cleanup();
+        return st;
+    }
+    cleanup();
+    if (stats_out) {
+        *stats_out = rs;
+        stats_out->copies += inner.copies;
+        stats_out->h2d_bytes += inner.h2d_bytes;
+        stats_out->d2h_bytes += inner.d2h_bytes;
+    }
+    *all_out = FutRef(reinterpret_cast<Future *>(all), true);
+    return HXC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1041,101 +1132,71 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dh, const double *host_u0, doubl
     hxc_status st = deps_from_handles(deps, ndeps, &dv);
     if (st) return st;
     if ((st = d->make_current())) return st;
-    const size_t field = (size_t)cfg->ny * cfg->nx * 8;
-    // the device field pair of this call, and the call that used it last
+    // the device field pair of this call, the call that used it last, and
+    // the promise the pair's next user orders itself after
     int slot;
-    FutRef prev;
+    FutRef prev, whole = make_pending();
     {
         std::lock_guard<std::mutex> g(g_hostrun_m);
         HostRunSlots &hs = g_hostrun[d.get()];
         slot = hs.next;
         hs.next ^= 1;
         prev = hs.last[slot];
+        hs.last[slot] = fut_order_only(whole);
     }
-    void *pu, *pt;
-    if ((st = d->scratch_get(kHostKeyU[slot], field, &pu))) return st;
-    if ((st = d->scratch_get(kHostKeyT[slot], field, &pt))) return st;
-    hxc_buffer ub, tb;
-    hxc_buffer_wrap(dh, pu, field, &ub);
-    hxc_buffer_wrap(dh, pt, field, &tb);
-    Tiles tl;
-    tl.TY = cfg->tiles_y;
-    tl.TX = cfg->tiles_x;
-    tl.by = split(cfg->ny, cfg->tiles_y, false);
-    tl.bx = split(cfg->nx, cfg->tiles_x, true);
-    const int64_t T = tl.count(), nx = cfg->nx;
-    hxc_run_stats inner{};
-    std::vector<hxc_future> in_deps;
-    for (auto &f : dv) in_deps.push_back(to_handle(f));
-    if (prev) in_deps.push_back(to_handle(prev));
-    std::vector<hxc_future> h2d, d2h;
-    hxc_future run = nullptr, ready = nullptr;
-    auto cleanup = [&]() {
-        for (auto f : in_deps) hxc_future_release(f);
-        for (auto f : h2d) hxc_future_release(f);
-        for (auto f : d2h) hxc_future_release(f);
-        if (run) hxc_future_release(run);
-        if (ready) hxc_future_release(ready);
-        hxc_buffer_release(ub);
-        hxc_buffer_release(tb);
-    };
-    // uploads and downloads on their own stream slots, so that they overlap
-    // the steps of the call issued before this one
-    for (int64_t t = 0; t < T && !st; t++) {
-        size_t off = ((size_t)tl.y0(t) * nx + tl.x0(t)) * 8;
-        hxc_future f = nullptr;
-        st = hxc_buffer_enqueue_write_2d(ub, off, nx * 8, (const char *)host_u0 + off, nx * 8,
-                                         tl.tx(t) * 8, tl.ty(t), kHostInSlot0 + (int)(t % kHostSlots),
-                                         in_deps.data(), (int)in_deps.size(), &f);
-        if (!st) h2d.push_back(f);
-        inner.copies++;
-        inner.h2d_bytes += tl.tx(t) * tl.ty(t) * 8;
+    if (prev) dv.push_back(prev);
+    if (has_pending_host(dv)) {
+        // unfinished host work ahead (typically the pair's last user, a call
+        // still running): the whole call is issued by the worker pool once
+        // every dependency is done, so that its uploads, steps and downloads
+        // are enqueued together.  Issued piecemeal (each copy as its own
+        // dependency came in, the downloads only after the field was done)
+        // back-to-back calls ran 432 instead of 418 ms per 8192^2 call.
+        auto c = std::make_shared<hxc_heat2d_cfg>(*cfg);
+        FutRef a = make_pending();
+        auto left = std::make_shared<std::atomic<int>>((int)dv.size());
+        auto failed = std::make_shared<std::atomic<int>>(0);
+        auto fire = [=]() {
+            if (failed->load()) {  // nothing is issued into the pair
+                fut_set_done(a, HXC_E_DEP_FAILED);
+                fut_set_done(whole, HXC_OK);
+                return;
+            }
+            pool().submit([=] {
+                FutRef all;
+                hxc_status s2 = d->make_current();
+                if (!s2)
+                    s2 = host_run_issue(dh, d.get(), slot, host_u0, host_uT, c.get(), {}, &all,
+                                        nullptr);
+                // the pair's next user waits for whatever was issued into it
+                if (all)
+                    fut_on_done(all, [whole](hxc_status s3) { fut_set_done(whole, s3); });
+                else
+                    fut_set_done(whole, HXC_OK);
+                if (s2) {
+                    fut_set_done(a, s2);
+                    return;
+                }
+                fut_on_done(all, [a](hxc_status s3) { fut_set_done(a, s3); });
+            });
+        };
+        for (auto &f : dv)
+            fut_on_done(f, [left, failed, fire](hxc_status s2) {
+                if (s2 != HXC_OK) failed->store(1);
+                if (left->fetch_sub(1) == 1) fire();
+            });
+        *out = to_handle(a);
+        return HXC_OK;
     }
-    hxc_run_stats rs{};
-    if (!st) st = heat2d_run_entry(dh, ub, tb, cfg, h2d.data(), (int)T, &run, &ready, &rs, true);
-    for (int64_t t = 0; t < T && !st; t++) {
-        size_t off = ((size_t)tl.y0(t) * nx + tl.x0(t)) * 8;
-        hxc_future f = nullptr;
-        st = hxc_buffer_enqueue_read_2d(ub, off, nx * 8, (char *)host_uT + off, nx * 8,
-                                        tl.tx(t) * 8, tl.ty(t), kHostOutSlot0 + (int)(t % kHostSlots),
-                                        &ready, 1, &f);
-        if (!st) d2h.push_back(f);
-        inner.copies++;
-        inner.d2h_bytes += tl.tx(t) * tl.ty(t) * 8;
-    }
-    hxc_future all = nullptr;
-    if (!st) {
-        d2h.push_back(run);
-        run = nullptr;
-        st = hxc_when_all(d2h.data(), (int)d2h.size(), &all);
-    }
-    if (st) {
-        // nothing more is issued into this pair; its next user waits for
-        // whatever did get issued
-        std::vector<hxc_future> issued(h2d);
-        issued.insert(issued.end(), d2h.begin(), d2h.end());
-        if (run) issued.push_back(run);
-        hxc_future j = nullptr;
-        if (!issued.empty() && hxc_when_all(issued.data(), (int)issued.size(), &j) == HXC_OK) {
-            std::lock_guard<std::mutex> g(g_hostrun_m);
-            g_hostrun[d.get()].last[slot] = fut_order_only(fut_from_handle(j));
-            hxc_future_release(j);
-        }
-        cleanup();
-        return st;
-    }
-    {
-        std::lock_guard<std::mutex> g(g_hostrun_m);
-        g_hostrun[d.get()].last[slot] = fut_order_only(fut_from_handle(all));
-    }
-    cleanup();
-    if (stats_out) {
-        *stats_out = rs;
-        stats_out->copies += inner.copies;
-        stats_out->h2d_bytes += inner.h2d_bytes;
-        stats_out->d2h_bytes += inner.d2h_bytes;
-    }
-    *out = all;
+    FutRef all;
+    st = host_run_issue(dh, d.get(), slot, host_u0, host_uT, cfg, dv, &all, stats_out);
+    // the pair's next user waits for whatever was issued into it
+    if (all)
+        fut_on_done(all, [whole](hxc_status s2) { fut_set_done(whole, s2); });
+    else
+        fut_set_done(whole, st ? st : HXC_OK);
+    if (st) return st;
+    *out = to_handle(all);
     return HXC_OK;
 }
 
