@@ -452,9 +452,9 @@ hxc_status hxc_heat1d_run(hxc_device dev, hxc_buffer u, hxc_buffer tmp, int64_t 
  * v' = fma((1-2r)/r, v, s), 2 FP64 operations per point; counts[2] closing
  * steps, u' = fma(r^(m+1), s, ((1-2r) r^m) v), 3 operations; counts[0]
  * canonical steps, t = fma(-2, u, s), u' = fma(r, t, u), 3 operations (every
- * step when r is outside (0, 1/2] or r^-1 > 2^48).  The intervals are of
+ * step when r is outside (0, 1/2] or r^-1 > 2^96).  The intervals are of
  * min(steps, 128) steps (what one captured graph holds), cut into groups of
- * at most M + 1 steps, M the largest m with r^-m <= 2^48 (24 at r = 1/4).
+ * at most M + 1 steps, M the largest m with r^-m <= 2^96 (48 at r = 1/4).
  * counts: 3 int64 written.  Host only, no device needed. */
 hxc_status hxc_heat1d_step_kinds(double r, int steps, int64_t *counts);
 
@@ -529,13 +529,13 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dev, const double *host_u0, doub
  * 3 FP64 operations per point; counts[2] "closing" steps back to true
  * values, u' = fma(r^(m+1), s, ((1-4r) r^m) v), 4 operations; counts[0]
  * canonical steps, t = fma(-4, u, s), u' = fma(r, t, u), 4 operations (every
- * step when r is outside (0, 1/4] or r^-1 > 2^48).  s is always
+ * step when r is outside (0, 1/4] or r^-1 > 2^96).  s is always
  * (uN + uW) + (uE + uS).  The steps are issued in intervals (snapshot_every
  * when snapshot norms are requested, else min(steps, 100)); each interval is
- * cut into groups of at most M + 1 steps, M the largest m with r^-m <= 2^48
- * (20 at r = 0.2), whose last step closes, so the field holds true values at
+ * cut into groups of at most M + 1 steps, M the largest m with r^-m <= 2^96
+ * (41 at r = 0.2), whose last step closes, so the field holds true values at
  * every snapshot and at the end.  The scaled field grows by at most 1/r per
- * step: inputs with |u| <= 2^975 stay finite.  counts: 3 int64 written.
+ * step: inputs with |u| <= 2^927 stay finite.  counts: 3 int64 written.
  * Host only, no device needed. */
 hxc_status hxc_heat2d_step_kinds(const hxc_heat2d_cfg *cfg, int64_t *counts);
 

@@ -21,7 +21,7 @@
 // M bounds the growth of the scaled field: for 0 < r <= 1/(2d) the scaled
 // step's coefficients (1 - 2d r)/r and 2d 1s are non-negative and sum to
 // 1/r, so |v| grows by at most 1/r per step; M is the largest m with
-// r^-m <= 2^48.  The scaled field of a field with |u| <= 2^975 therefore
+// r^-m <= 2^96.  The scaled field of a field with |u| <= 2^927 therefore
 // stays finite.  Outside 0 < r <= 1/(2d), or where M would be 0, every step
 // is the canonical one (t = fma(-2d, u, s), u' = fma(r, t, u)).
 #pragma once
@@ -40,12 +40,12 @@ namespace drv {
 // dimensions (0: none).
 inline int ftcs_max_scaled(int dim, double r) {
     if (!(r > 0.0 && r <= 0.5 / dim)) return 0;
-    // largest m with r^m >= 2^-48 (exact for powers of two such as 1/4)
+    // largest m with r^m >= 2^-96 (exact for powers of two such as 1/4)
     long double p = 1.0L;
     int m = 0;
     while (m < k::kFtcsMaxGroup - 1) {
         p *= (long double)r;
-        if (p < 0x1p-48L) break;
+        if (p < 0x1p-96L) break;
         m++;
     }
     return m;

@@ -66,7 +66,7 @@ struct FtcsStep {
 // groups of P steps (the last shorter) whose last step closes; the others
 // are scaled.  P = 0: every step canonical with r.  The closing step after q
 // scaled steps uses a[q], b[q].
-constexpr int kFtcsMaxGroup = 65;
+constexpr int kFtcsMaxGroup = 97;
 struct FtcsPlan {
     double r, k;
     int P, I;

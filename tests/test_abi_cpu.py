@@ -298,22 +298,23 @@ def test_host_run_and_graph_calls_reject_bad_arguments(L):
 
 
 @pytest.mark.parametrize("r,steps,every,norms,want", [
-    # r = 0.2: at most 20 scaled steps in a row (0.2^-20 <= 2^48 < 0.2^-21), so
-    # an interval of 100 steps is 5 groups (4 x 21 + 16), each closed once
-    (0.2, 1000, 100, True, (0, 950, 50)),
-    (0.2, 1000, 100, False, (0, 950, 50)),  # no norms: intervals of 100 all the same
-    (0.2, 200, 0, False, (0, 190, 10)),
-    (0.2, 22, 0, False, (0, 20, 2)),        # 21 + 1
-    (0.2, 21, 0, False, (0, 20, 1)),
+    # r = 0.2: at most 41 scaled steps in a row (0.2^-41 <= 2^96 < 0.2^-42), so
+    # an interval of 100 steps is 3 groups (42 + 42 + 16), each closed once
+    (0.2, 1000, 100, True, (0, 970, 30)),
+    (0.2, 1000, 100, False, (0, 970, 30)),  # no norms: intervals of 100 all the same
+    (0.2, 200, 0, False, (0, 194, 6)),
+    (0.2, 43, 0, False, (0, 41, 2)),        # 42 + 1
+    (0.2, 42, 0, False, (0, 41, 1)),
     (0.2, 1000, 1, True, (0, 0, 1000)),     # a snapshot after every step
     (0.2, 10, 3, True, (0, 6, 4)),          # intervals 3, 3, 3 (2 scaled + 1) and a last 1
-    # r = 1/4: (1/4)^24 = 2^-48 exactly, so 24 scaled steps: 100 = 4 x 25
-    (0.25, 100, 0, False, (0, 96, 4)),
-    # r = 0.01: 7 (0.01^-7 = 1e14 <= 2^48 < 1e16): 250 = 100 + 100 + 50,
-    # 13 + 13 + 7 groups of at most 8
-    (0.01, 250, 0, False, (0, 217, 33)),
+    # r = 1/4: (1/4)^48 = 2^-96 exactly, so 48 scaled steps: 100 = 49 + 49 + 2
+    (0.25, 100, 0, False, (0, 97, 3)),
+    # r = 0.01: 14 (0.01^-14 = 1e28 <= 2^96 < 1e30): 250 = 100 + 100 + 50,
+    # 7 + 7 + 4 groups of at most 15
+    (0.01, 250, 0, False, (0, 232, 18)),
+    (1e-17, 10, 0, False, (0, 5, 5)),       # 1e17 <= 2^96 < 1e34: groups of 2
     (0.3, 50, 0, False, (50, 0, 0)),        # beyond the stability bound: canonical
-    (1e-17, 10, 0, False, (10, 0, 0)),      # one scaled step would grow 1e17 > 2^48
+    (1e-30, 10, 0, False, (10, 0, 0)),      # one scaled step would grow 1e30 > 2^96
     (-0.1, 5, 0, False, (5, 0, 0)),
     (0.2, 0, 0, False, (0, 0, 0)),
 ])
@@ -332,16 +333,16 @@ def test_heat2d_step_kinds_arguments(L):
 
 
 @pytest.mark.parametrize("r,steps,want", [
-    # r = 1/4: (1/4)^24 = 2^-48, so 24 scaled steps in a row; an interval of
-    # 100 steps is 4 groups of 25
-    (0.25, 100, (0, 96, 4)),
-    # 300 steps: intervals of 128, 128, 44; 6 + 6 + 2 groups
-    (0.25, 300, (0, 286, 14)),
+    # r = 1/4: (1/4)^48 = 2^-96, so 48 scaled steps in a row; an interval of
+    # 100 steps is 3 groups (49 + 49 + 2)
+    (0.25, 100, (0, 97, 3)),
+    # 300 steps: intervals of 128, 128, 44; 3 + 3 + 1 groups
+    (0.25, 300, (0, 293, 7)),
     (0.25, 1, (0, 0, 1)),
-    # r = 1/2: (1 - 2r)/r = 0, 48 scaled steps in a row: 100 = 49 + 49 + 2
-    (0.5, 100, (0, 97, 3)),
+    # r = 1/2: (1 - 2r)/r = 0, 96 scaled steps in a row: 100 = 97 + 3
+    (0.5, 100, (0, 98, 2)),
     (0.6, 10, (10, 0, 0)),     # beyond the stability bound: canonical
-    (1e-17, 10, (10, 0, 0)),   # one scaled step would grow 1e17 > 2^48
+    (1e-30, 10, (10, 0, 0)),   # one scaled step would grow 1e30 > 2^96
     (0.25, 0, (0, 0, 0)),
 ])
 def test_heat1d_step_kinds(L, r, steps, want):
