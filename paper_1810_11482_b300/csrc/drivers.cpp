@@ -1132,6 +1132,7 @@ hxc_status hxc_heat2d_run_host_async(hxc_device dh, const double *host_u0, doubl
     hxc_status st = deps_from_handles(deps, ndeps, &dv);
     if (st) return st;
     if ((st = d->make_current())) return st;
+    if (stats_out) memset(stats_out, 0, sizeof *stats_out);
     // the device field pair of this call, the call that used it last, and
     // the promise the pair's next user orders itself after
     int slot;
