@@ -342,25 +342,42 @@ hxc_status issue_steps2d(Heat2dRun &R, int64_t s0, int64_t s1, std::vector<FutRe
                          bool fused) {
     const hxc_heat2d_cfg &c = *R.cfg;
     const int64_t T = R.tl.count();
+    if (fused && s1 > s0) {
+        // the interval's whole-field steps as one operation: back-to-back
+        // launches, each after the first with programmatic dependent launch
+        // (its CTAs are placed while the step ahead of it drains)
+        std::vector<FutRef> deps;
+        for (auto &f : prev)
+            if (f) {
+                deps.push_back(f);
+                break;  // in fused mode every tile holds the same future
+            }
+        double *b0 = R.buf[0], *b1 = R.buf[1];
+        const int64_t ny = c.ny, nx = c.nx;
+        const double r = c.r;
+        FutRef f;
+        hxc_status st = issue_device_op(
+            R.dev, 0, deps,
+            [=](cudaStream_t q) {
+                for (int64_t s = s0; s < s1; s++) {
+                    const double *src = s % 2 ? b1 : b0;
+                    double *dst = s % 2 ? b0 : b1;
+                    cudaError_t e = k::heat2d_step(src, dst, ny, nx, 0, 0, ny, nx,
+                                                   ftcs2_step(r, s - s0, s1 - s0), 0, q, s > s0);
+                    if (e != cudaSuccess) return e;
+                }
+                return cudaSuccess;
+            },
+            {}, &f);
+        if (st) return st;
+        R.stats.launch(s1 - s0);
+        for (auto &p : prev) p = f;
+        return HXC_OK;
+    }
     for (int64_t s = s0; s < s1; s++) {
         const double *src = R.buf[s % 2];
         double *dst = R.buf[(s + 1) % 2];
         const k::FtcsStep kind = ftcs2_step(c.r, s - s0, s1 - s0);
-        if (fused) {
-            std::vector<FutRef> deps;
-            for (auto &f : prev)
-                if (f) deps.push_back(f);
-            FutRef f;
-            int64_t ny = c.ny, nx = c.nx;
-            hxc_status st = issue_device_op(
-                R.dev, 0, deps,
-                [=](cudaStream_t st) { return k::heat2d_step(src, dst, ny, nx, 0, 0, ny, nx, kind, 0, st); },
-                {}, &f);
-            if (st) return st;
-            R.stats.launch();
-            for (auto &p : prev) p = f;
-            continue;
-        }
         std::vector<FutRef> cur(T);
         for (int64_t t = 0; t < T; t++) {
             std::vector<FutRef> deps;

@@ -325,6 +325,13 @@ __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__
                                                 double *__restrict__ dst, int64_t ny, int64_t nx,
                                                 int64_t y0, int64_t x0, int64_t ty, int64_t tx,
                                                 double c0, double c1, int H, double one) {
+    // Programmatic dependent launch: a launch that may start before the
+    // kernel ahead of it on the stream has finished waits for it (and for its
+    // memory) before touching global memory, then lets the next launch place
+    // its CTAs as room frees up.  Launched without that attribute, both are
+    // no-ops.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t SW = 32 * V;
@@ -403,10 +410,28 @@ void set_heat2d_occupancy(int v) { tune::set("heat2d.occupancy", v); }
 
 namespace {
 
+// Launches `kernel` with the programmatic-dependent-launch attribute when
+// `pdl` (the kernel ahead of it on the stream may still be running).
+template <typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Args...), unsigned g, unsigned b, cudaStream_t s, bool pdl,
+                       Args... args) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(g);
+    lc.blockDim = dim3(b);
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, kernel, args...);
+}
+
 template <int M>
 cudaError_t heat2d_launch(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                           int64_t x0, int64_t ty, int64_t tx, double c0, double c1,
-                          int rows_per_warp, const hxc_launch_cfg *cfg, cudaStream_t s) {
+                          int rows_per_warp, const hxc_launch_cfg *cfg, cudaStream_t s,
+                          bool pdl = false) {
     if (ty <= 0 || tx <= 0) return cudaSuccess;
     const int H = rows_per_warp > 0 ? rows_per_warp : heat2d_rows();
     const bool vec = (nx % 2 == 0) && (x0 % 2 == 0) && (tx % 2 == 0) &&
@@ -420,32 +445,30 @@ cudaError_t heat2d_launch(const double *src, double *dst, int64_t ny, int64_t nx
     // (0..4: points a and b of a lane take floor/ceil of half of it), and
     // the minimum resident CTAs per SM the kernel is compiled for (4..6)
     const int em = heat2d_emul(), occ = heat2d_occupancy();
-#define HXC_L2D(VV, A, B, MB) \
-    k_heat2d<VV, A, B, MB, M><<<g, b, 0, s>>>(src, dst, ny, nx, y0, x0, ty, tx, c0, c1, H, 1.0)
+#define HXC_L2D(VV, A, B, MB)                                                                 \
+    return launch_pdl(k_heat2d<VV, A, B, MB, M>, g, b, s, pdl, src, dst, ny, nx, y0, x0, ty, tx, \
+                      c0, c1, H, 1.0)
     if (!vec) {
         switch (em / 2) {
-            case 0: HXC_L2D(1, 0, 0, 4); break;
-            case 1: HXC_L2D(1, 1, 1, 4); break;
-            default: HXC_L2D(1, 2, 2, 4); break;
+            case 0: HXC_L2D(1, 0, 0, 4);
+            case 1: HXC_L2D(1, 1, 1, 4);
+            default: HXC_L2D(1, 2, 2, 4);
         }
-        return cudaGetLastError();
     }
     if (em == 0) {
         switch (occ) {
-            case 5: HXC_L2D(2, 0, 0, 5); break;
-            case 6: HXC_L2D(2, 0, 0, 6); break;
-            default: HXC_L2D(2, 0, 0, 4); break;
+            case 5: HXC_L2D(2, 0, 0, 5);
+            case 6: HXC_L2D(2, 0, 0, 6);
+            default: HXC_L2D(2, 0, 0, 4);
         }
-        return cudaGetLastError();
     }
     switch (em) {
-        case 1: HXC_L2D(2, 0, 1, 4); break;
-        case 2: HXC_L2D(2, 1, 1, 4); break;
-        case 3: HXC_L2D(2, 1, 2, 4); break;
-        default: HXC_L2D(2, 2, 2, 4); break;
+        case 1: HXC_L2D(2, 0, 1, 4);
+        case 2: HXC_L2D(2, 1, 1, 4);
+        case 3: HXC_L2D(2, 1, 2, 4);
+        default: HXC_L2D(2, 2, 2, 4);
     }
 #undef HXC_L2D
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -459,17 +482,17 @@ cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64
 
 cudaError_t heat2d_step(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                         int64_t x0, int64_t ty, int64_t tx, const FtcsStep &step,
-                        int rows_per_warp, cudaStream_t s) {
+                        int rows_per_warp, cudaStream_t s, bool pdl) {
     switch (step.kind) {
         case kFtcsScaled:
             return heat2d_launch<kFtcsScaled>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
-                                               rows_per_warp, nullptr, s);
+                                               rows_per_warp, nullptr, s, pdl);
         case kFtcsClose:
             return heat2d_launch<kFtcsClose>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
-                                              rows_per_warp, nullptr, s);
+                                              rows_per_warp, nullptr, s, pdl);
         default:
             return heat2d_launch<kFtcsCanon>(src, dst, ny, nx, y0, x0, ty, tx, step.c0, step.c1,
-                                              rows_per_warp, nullptr, s);
+                                              rows_per_warp, nullptr, s, pdl);
     }
 }
 

@@ -90,9 +90,11 @@ constexpr int kHeat1dMaxSteps = 1024;
 cudaError_t heat2d(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                    int64_t x0, int64_t ty, int64_t tx, double r, int rows_per_warp,
                    const hxc_launch_cfg *cfg, cudaStream_t s);
+// One 2D step of kind `step`; `pdl`: launched with programmatic dependent
+// launch, for a launch that directly follows another step kernel on `s`.
 cudaError_t heat2d_step(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,
                         int64_t x0, int64_t ty, int64_t tx, const FtcsStep &step,
-                        int rows_per_warp, cudaStream_t s);
+                        int rows_per_warp, cudaStream_t s, bool pdl = false);
 
 // 2D kernel knobs (tuning registry): share of the additions run on the
 // integer pipe (half-additions per point, 0..6), rows per warp, compiled
