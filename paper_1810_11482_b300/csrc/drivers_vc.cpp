@@ -333,16 +333,25 @@ hxc_status hxc_varcoef_forward_run(hxc_device dh, hxc_buffer u0h, hxc_buffer kh,
         return st;
     stats.launch();
     f = g;
-    // the last step writes uT: the states alternate between W and uT
-    for (int t = 0; t < steps; t++) {
-        const bool to_T = ((steps - 1 - t) % 2) == 0;
-        const double *src = t == 0 ? U0 : (to_T ? W : UT);
-        double *dst = to_T ? UT : W;
+    // the last step writes uT: the states alternate between W and uT.  The
+    // steps are one operation: back-to-back launches, each after the first
+    // with programmatic dependent launch
+    if (steps > 0) {
         if ((st = issue_device_op(dev, 0, one(f),
-                                  [=](cudaStream_t q) { return k::vc_step(src, dst, WE, WS, M, ny, nx, q); },
+                                  [=](cudaStream_t q) {
+                                      for (int t = 0; t < steps; t++) {
+                                          const bool to_T = ((steps - 1 - t) % 2) == 0;
+                                          const double *src = t == 0 ? U0 : (to_T ? W : UT);
+                                          double *dst = to_T ? UT : W;
+                                          cudaError_t e =
+                                              k::vc_step(src, dst, WE, WS, M, ny, nx, q, t > 0);
+                                          if (e != cudaSuccess) return e;
+                                      }
+                                      return cudaSuccess;
+                                  },
                                   {}, &g)))
             return st;
-        stats.launch();
+        stats.launch(steps);
         f = g;
     }
     if (steps == 0 && UT != U0) {
@@ -481,6 +490,27 @@ hxc_status adjoint_impl(hxc_device dh, hxc_buffer u0h, hxc_buffer tapeh, hxc_buf
             if (!s3) f = g;
             return s3;
         };
+        // FUSED and GRAPH issue each run of kernel launches as one operation,
+        // the launches after the first with programmatic dependent launch;
+        // PLAIN issues every launch as an operation of its own
+        using Launch = std::function<cudaError_t(cudaStream_t, bool)>;
+        std::vector<Launch> pend;
+        auto flush = [&]() -> hxc_status {
+            if (pend.empty()) return HXC_OK;
+            auto ks = std::make_shared<std::vector<Launch>>(std::move(pend));
+            pend.clear();
+            return op([ks](cudaStream_t q) {
+                for (size_t i = 0; i < ks->size(); i++) {
+                    cudaError_t e = (*ks)[i](q, i > 0);
+                    if (e != cudaSuccess) return e;
+                }
+                return cudaSuccess;
+            });
+        };
+        auto kern = [&](Launch l) -> hxc_status {
+            pend.push_back(std::move(l));
+            return mode == HXC_MODE_PLAIN ? flush() : HXC_OK;
+        };
         if ((s2 = op([=](cudaStream_t q) { return k::vc_coef(K, c, ny, nx, WE, WS, M, q); }))) return s2;
         sc.launch();
         // forward: states pass through the work fields; segment starts go to
@@ -497,10 +527,14 @@ hxc_status adjoint_impl(hxc_device dh, hxc_buffer u0h, hxc_buffer tapeh, hxc_buf
                 dst = WK + (size_t)((t + 1) & 1) * n;
             if (dst == cur) dst = WK + (size_t)(((t + 1) & 1) ^ 1) * n;
             const double *src = cur;
-            if ((s2 = op([=](cudaStream_t q) { return k::vc_step(src, dst, WE, WS, M, ny, nx, q); }))) return s2;
+            if ((s2 = kern([=](cudaStream_t q, bool pdl) {
+                     return k::vc_step(src, dst, WE, WS, M, ny, nx, q, pdl);
+                 })))
+                return s2;
             sc.launch();
             cur = dst;
         }
+        if ((s2 = flush())) return s2;
         // adjoint seed and the per-face gradient sums
         if ((s2 = op([=](cudaStream_t q) {
                  cudaError_t e = cudaMemcpyAsync(LM, LT, nb, cudaMemcpyDeviceToDevice, q);
@@ -515,7 +549,9 @@ hxc_status adjoint_impl(hxc_device dh, hxc_buffer u0h, hxc_buffer tapeh, hxc_buf
             for (int t = n0; t + 1 < n1; t++) {
                 const double *src = t == n0 ? ckpt(kk) : SEG + (size_t)(t - n0) * n;
                 double *dst = SEG + (size_t)(t + 1 - n0) * n;
-                if ((s2 = op([=](cudaStream_t q) { return k::vc_step(src, dst, WE, WS, M, ny, nx, q); })))
+                if ((s2 = kern([=](cudaStream_t q, bool pdl) {
+                         return k::vc_step(src, dst, WE, WS, M, ny, nx, q, pdl);
+                     })))
                     return s2;
                 sc.launch();
             }
@@ -524,18 +560,21 @@ hxc_status adjoint_impl(hxc_device dh, hxc_buffer u0h, hxc_buffer tapeh, hxc_buf
                 const double *lin = LM + (size_t)li * n;
                 double *lout = (t == 0) ? GU : LM + (size_t)(li ^ 1) * n;
                 if (mode == HXC_MODE_PLAIN) {
-                    if ((s2 = op([=](cudaStream_t q) {
-                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, false, true, q);
+                    if ((s2 = kern([=](cudaStream_t q, bool pdl) {
+                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, false, true,
+                                                  q, pdl);
                          })))
                         return s2;
-                    if ((s2 = op([=](cudaStream_t q) {
-                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, true, false, q);
+                    if ((s2 = kern([=](cudaStream_t q, bool pdl) {
+                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, true, false,
+                                                  q, pdl);
                          })))
                         return s2;
                     sc.launch(2);
                 } else {
-                    if ((s2 = op([=](cudaStream_t q) {
-                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, true, true, q);
+                    if ((s2 = kern([=](cudaStream_t q, bool pdl) {
+                             return k::vc_adjoint(lin, lout, ut, WE, WS, M, FACE, ny, nx, true, true,
+                                                  q, pdl);
                          })))
                         return s2;
                     sc.launch();
@@ -543,6 +582,7 @@ hxc_status adjoint_impl(hxc_device dh, hxc_buffer u0h, hxc_buffer tapeh, hxc_buf
                 li ^= 1;
             }
         }
+        if ((s2 = flush())) return s2;
         if (steps > 0) {
             // dL/dkappa from the face sums
             if ((s2 = op([=](cudaStream_t q) { return k::vc_face_combine(FACE, GK, c, ny, nx, q); })))
@@ -702,7 +742,9 @@ hxc_status hxc_varcoef_forward_tape(hxc_device dh, hxc_buffer u0h, hxc_buffer kh
     stats.launch();
     // the same sequence of states as the adjoint run's own forward pass:
     // segment starts into the tape, the final state into uT, the others
-    // through two work fields
+    // through two work fields; the steps are one operation, back-to-back
+    // launches, each after the first with programmatic dependent launch
+    auto seq = std::make_shared<std::vector<std::pair<const double *, double *>>>();
     const double *cur = TP;
     for (int t = 0; t < steps; t++) {
         double *dst;
@@ -713,11 +755,20 @@ hxc_status hxc_varcoef_forward_tape(hxc_device dh, hxc_buffer u0h, hxc_buffer kh
         else
             dst = WK + (size_t)((t + 1) & 1) * n;
         if (dst == cur) dst = WK + (size_t)(((t + 1) & 1) ^ 1) * n;
-        const double *src = cur;
-        if ((st = op([=](cudaStream_t q) { return k::vc_step(src, dst, WE, WS, M, ny, nx, q); })))
-            return st;
-        stats.launch();
+        seq->push_back({cur, dst});
         cur = dst;
+    }
+    if (steps > 0) {
+        if ((st = op([=](cudaStream_t q) {
+                 for (size_t t = 0; t < seq->size(); t++) {
+                     cudaError_t e = k::vc_step((*seq)[t].first, (*seq)[t].second, WE, WS, M, ny, nx,
+                                                q, t > 0);
+                     if (e != cudaSuccess) return e;
+                 }
+                 return cudaSuccess;
+             })))
+            return st;
+        stats.launch(steps);
     }
     if (steps == 0 &&
         (st = op([=](cudaStream_t q) {

@@ -23,6 +23,7 @@
 // schedules, steps per launch and graph replay holds for them too.
 #include "fp64_int.cuh"
 #include "kernels.cuh"
+#include "pdl.cuh"
 #include "tune.hpp"
 
 #include <algorithm>
@@ -325,13 +326,7 @@ __global__ void __launch_bounds__(256, MINB) k_heat2d(const double *__restrict__
                                                 double *__restrict__ dst, int64_t ny, int64_t nx,
                                                 int64_t y0, int64_t x0, int64_t ty, int64_t tx,
                                                 double c0, double c1, int H, double one) {
-    // Programmatic dependent launch: a launch that may start before the
-    // kernel ahead of it on the stream has finished waits for it (and for its
-    // memory) before touching global memory, then lets the next launch place
-    // its CTAs as room frees up.  Launched without that attribute, both are
-    // no-ops.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_prologue();  // launched back to back with programmatic dependent launch
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t SW = 32 * V;
@@ -409,23 +404,6 @@ int heat2d_occupancy() { return (int)tune::get("heat2d.occupancy"); }
 void set_heat2d_occupancy(int v) { tune::set("heat2d.occupancy", v); }
 
 namespace {
-
-// Launches `kernel` with the programmatic-dependent-launch attribute when
-// `pdl` (the kernel ahead of it on the stream may still be running).
-template <typename... Args>
-cudaError_t launch_pdl(void (*kernel)(Args...), unsigned g, unsigned b, cudaStream_t s, bool pdl,
-                       Args... args) {
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(g);
-    lc.blockDim = dim3(b);
-    lc.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    lc.attrs = at;
-    lc.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&lc, kernel, args...);
-}
 
 template <int M>
 cudaError_t heat2d_launch(const double *src, double *dst, int64_t ny, int64_t nx, int64_t y0,

@@ -33,6 +33,7 @@
 // boundary), S = GS[a] (x2 on the south boundary), N = GS[a-nx] (x2 GN0[j]
 // on the north boundary).  Per cell and step: 6 FP64 operations.
 #include "kernels.cuh"
+#include "pdl.cuh"
 #include "tune.hpp"
 
 #include <algorithm>
@@ -106,6 +107,7 @@ __global__ void k_vc_coef(const double *__restrict__ kap, double c, int64_t ny, 
 __global__ void k_vc_step(const double *__restrict__ u, double *__restrict__ un,
                           const double *__restrict__ wE, const double *__restrict__ wS,
                           const double *__restrict__ m, int64_t ny, int64_t nx, Fk f) {
+    pdl_prologue();
     // warps walk rows: lanes cover consecutive columns (coalesced)
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
@@ -124,6 +126,7 @@ __global__ void k_vc_step(const double *__restrict__ u, double *__restrict__ un,
 __global__ void k_vc_step2(const double *__restrict__ u, double *__restrict__ un,
                            const double *__restrict__ wE, const double *__restrict__ wS,
                            const double *__restrict__ m, int64_t ny, int64_t nx, Fk f) {
+    pdl_prologue();
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t segs = (nx + 63) / 64;
@@ -217,6 +220,7 @@ __global__ void k_vc_adjoint(const double *__restrict__ lam, double *__restrict_
                              const double *__restrict__ wS, const double *__restrict__ m,
                              double *face, int64_t ny, int64_t nx, int do_lam, int do_grad,
                              Fk f) {
+    pdl_prologue();
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t segs = (nx + 31) / 32;
@@ -478,7 +482,7 @@ cudaError_t vc_coef(const double *kap, double c, int64_t ny, int64_t nx, double 
 }
 
 cudaError_t vc_step(const double *u, double *un, const double *wE, const double *wS,
-                    const double *m, int64_t ny, int64_t nx, cudaStream_t s) {
+                    const double *m, int64_t ny, int64_t nx, cudaStream_t s, bool pdl) {
     const bool vec = nx % 2 == 0 && reinterpret_cast<uintptr_t>(u) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(un) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(wE) % 16 == 0 &&
@@ -486,12 +490,12 @@ cudaError_t vc_step(const double *u, double *un, const double *wE, const double 
                      reinterpret_cast<uintptr_t>(m) % 16 == 0;
     if (vec) {
         const int64_t work2 = ny * ((nx + 63) / 64);
-        k_vc_step2<<<grid_for(work2, 8, nullptr), 256, 0, s>>>(u, un, wE, wS, m, ny, nx, kF);
-        return cudaGetLastError();
+        return launch_pdl(k_vc_step2, grid_for(work2, 8, nullptr), 256, s, pdl, u, un, wE, wS, m,
+                          ny, nx, kF);
     }
     const int64_t work = ny * ((nx + 31) / 32);
-    k_vc_step<<<grid_for(work, 8, nullptr), 256, 0, s>>>(u, un, wE, wS, m, ny, nx, kF);
-    return cudaGetLastError();
+    return launch_pdl(k_vc_step, grid_for(work, 8, nullptr), 256, s, pdl, u, un, wE, wS, m, ny, nx,
+                      kF);
 }
 
 cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c, int64_t ny,
@@ -503,11 +507,10 @@ cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c
 
 cudaError_t vc_adjoint(const double *lam, double *lam_out, const double *u, const double *wE,
                        const double *wS, const double *m, double *face, int64_t ny, int64_t nx,
-                       bool do_lam, bool do_grad, cudaStream_t s) {
+                       bool do_lam, bool do_grad, cudaStream_t s, bool pdl) {
     const int64_t work = ny * ((nx + 31) / 32);
-    k_vc_adjoint<<<grid_for(work, 8, nullptr), 256, 0, s>>>(lam, lam_out, u, wE, wS, m, face, ny,
-                                                          nx, do_lam, do_grad, kF);
-    return cudaGetLastError();
+    return launch_pdl(k_vc_adjoint, grid_for(work, 8, nullptr), 256, s, pdl, lam, lam_out, u, wE,
+                      wS, m, face, ny, nx, (int)do_lam, (int)do_grad, kF);
 }
 
 size_t vc_face_doubles(int64_t ny, int64_t nx) { return (size_t)(2 * ny * nx + ny + nx); }

@@ -135,8 +135,10 @@ cudaError_t heat3d_wait_errors(unsigned *flags);
 // fly), adjoint step with kappa-gradient, squared-error seed, batches.
 cudaError_t vc_coef(const double *kap, double c, int64_t ny, int64_t nx, double *wE, double *wS,
                     double *m, cudaStream_t s);
+// `pdl`: launched with programmatic dependent launch, for a launch that
+// directly follows another step kernel on `s` (pdl.cuh).
 cudaError_t vc_step(const double *u, double *un, const double *wE, const double *wS,
-                    const double *m, int64_t ny, int64_t nx, cudaStream_t s);
+                    const double *m, int64_t ny, int64_t nx, cudaStream_t s, bool pdl = false);
 cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c, int64_t ny,
                         int64_t nx, const hxc_launch_cfg *cfg, cudaStream_t s);
 // Adjoint step (do_lam) and per-face kappa-gradient accumulation (do_grad)
@@ -145,7 +147,7 @@ cudaError_t vc_step_otf(const double *u, double *un, const double *kap, double c
 // sums into gk after the last step.
 cudaError_t vc_adjoint(const double *lam, double *lam_out, const double *u, const double *wE,
                        const double *wS, const double *m, double *face, int64_t ny, int64_t nx,
-                       bool do_lam, bool do_grad, cudaStream_t s);
+                       bool do_lam, bool do_grad, cudaStream_t s, bool pdl = false);
 size_t vc_face_doubles(int64_t ny, int64_t nx);
 cudaError_t vc_face_combine(const double *face, double *gk, double c, int64_t ny, int64_t nx,
                             cudaStream_t s);
