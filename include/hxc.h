@@ -228,7 +228,8 @@ typedef enum {
     /* Sec. 5.1.1: out_i = 0.5 in_{i-1} + in_i + 0.5 in_{i+1}, periodic. */
     HXC_K_PRK_STENCIL = 2,
     /* 1D FTCS: dst[lo, lo+count) = `steps` periodic steps of src.  steps > 1
-     * reads a halo of width `steps` from src (temporal blocking). */
+     * reads a halo of width `steps` from src (temporal blocking).  Every
+     * point rounds t = fma(-2, u, ul + ur), u' = fma(r, t, u) in FP64. */
     HXC_K_HEAT1D = 3,
     /* 2D FTCS step on the tile [y0, y0+ty) x [x0, x0+tx), zero outside the
      * field; every point rounds t = fma(-4, u, (uN + uW) + (uE + uS)),
