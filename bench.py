@@ -389,7 +389,7 @@ def ours(args, world, rank, local, pg):
         norm_sets = [(np.zeros(nsnap * T), np.zeros(nsnap * T)) for _ in range(2)]
         cfgs = [hxc.heat2d_cfg(NY, NX, TILES[0], TILES[1], R2D, STEPS2D, EVERY, best_mode, a, b)
                 for a, b in norm_sets]
-        k = max(2, min(args.steps, 5))
+        k = max(2, min(args.steps, 20))  # the steps of the resident loop (at most 20)
         for i in range(2):  # warm-up: both device field pairs allocated
             f, _ = hxc.heat2d_run_host_async(dev, hu.ctypes.data, hos[i].ctypes.data, cfgs[i])
             f.get()
