@@ -60,22 +60,7 @@ inline void ftcs_close_coef(int dim, double r, int q, double *a, double *b) {
     *b = (double)(c * rho);
 }
 
-// Kind and coefficients of step j (0-based) of an interval of L steps.
-inline k::FtcsStep ftcs_step(int dim, double r, int64_t j, int64_t L) {
-    const int M = ftcs_max_scaled(dim, r);
-    if (M == 0) return {k::kFtcsCanon, r, 0.0};
-    const int64_t P = (int64_t)M + 1, q = j % P, end = std::min<int64_t>(L, j - q + P);
-    if (j + 1 < end) {
-        const long double rl = r;
-        return {k::kFtcsScaled, (double)((1.0L - 2.0L * dim * rl) / rl), 0.0};
-    }
-    k::FtcsStep st{k::kFtcsClose, 0.0, 0.0};
-    ftcs_close_coef(dim, r, (int)q, &st.c0, &st.c1);
-    return st;
-}
-inline k::FtcsStep ftcs2_step(double r, int64_t j, int64_t L) { return ftcs_step(2, r, j, L); }
-
-// The plan the 1D launches of a run evaluate (same kinds and coefficients as
+// The plan of the launches of a run (same kinds and coefficients as
 // ftcs_step): a run of `total` steps in intervals of `interval`.
 inline k::FtcsPlan ftcs_plan(int dim, double r, int64_t total, int64_t interval) {
     k::FtcsPlan p{};
@@ -91,6 +76,12 @@ inline k::FtcsPlan ftcs_plan(int dim, double r, int64_t total, int64_t interval)
     }
     return p;
 }
+
+// Kind and coefficients of step j (0-based) of an interval of L steps.
+inline k::FtcsStep ftcs_step(int dim, double r, int64_t j, int64_t L) {
+    return k::ftcs_plan_step(ftcs_plan(dim, r, L, L), j);
+}
+inline k::FtcsStep ftcs2_step(double r, int64_t j, int64_t L) { return ftcs_step(2, r, j, L); }
 
 // Interval length of a run of hxc_heat2d_run (0 when there are no steps).
 inline int64_t heat2d_interval(const hxc_heat2d_cfg &c) {

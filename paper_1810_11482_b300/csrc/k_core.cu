@@ -81,17 +81,6 @@ __device__ __forceinline__ double ftcs3(double ul, double u, double ur, double c
     }
 }
 
-// Kind and coefficients of run step g under `p` (the rule of ftcs_step,
-// evaluated from the plan's table, on either side).
-__host__ __device__ __forceinline__ FtcsStep plan_step(const FtcsPlan &p, int64_t g) {
-    if (p.P == 0) return {kFtcsCanon, p.r, 0.0};
-    const int64_t j = g % p.I, s0 = g - j;
-    const int64_t L = p.total - s0 < p.I ? p.total - s0 : (int64_t)p.I;
-    const int64_t q = j % p.P, end = L < j - q + p.P ? L : j - q + p.P;
-    if (j + 1 < end) return {kFtcsScaled, p.k, 0.0};
-    return {kFtcsClose, p.a[q], p.b[q]};
-}
-
 // One 2D pair sum (uE + uS of a point, = uN + uW of the point below and to
 // the right), on the integer-pipe adder when E >= 1.
 template <int E>
@@ -208,7 +197,7 @@ __global__ void k_heat1d_tb(const double *__restrict__ src, double *__restrict__
         __syncthreads();
         double *pa = a, *pb = b;
         for (int s = 1; s <= T; s++) {
-            const FtcsStep st = plan_step(plan, g0 + s - 1);  // uniform per level
+            const FtcsStep st = ftcs_plan_step(plan, g0 + s - 1);  // uniform per level
             if (st.kind == kFtcsScaled) {
                 for (int i = s + threadIdx.x; i < W - s; i += blockDim.x)
                     pb[i] = ftcs3<kFtcsScaled>(pa[i - 1], pa[i], pa[i + 1], st.c0, st.c1, one);
@@ -237,7 +226,7 @@ cudaError_t heat1d_plan(const double *src, double *dst, int64_t n, int64_t lo, i
     if (steps == 1) {
         unsigned b = block_from(cfg, 256);
         unsigned g = grid_from(cfg, std::min<int64_t>((count + b - 1) / b, sm_count() * 8));
-        const FtcsStep st = plan_step(plan, g0);  // decided on the host
+        const FtcsStep st = ftcs_plan_step(plan, g0);  // decided on the host
         switch (st.kind) {
             case kFtcsScaled:
                 k_heat1d_step<kFtcsScaled><<<g, b, 0, s>>>(src, dst, n, lo, count, st.c0, st.c1, 1.0);

@@ -74,6 +74,23 @@ struct FtcsPlan {
     double a[kFtcsMaxGroup], b[kFtcsMaxGroup];
 };
 
+#ifdef __CUDACC__
+#define HXC_HD __host__ __device__
+#else
+#define HXC_HD
+#endif
+// Kind and coefficients of run step g under plan p (the one rule, for the
+// host and the device).
+HXC_HD inline FtcsStep ftcs_plan_step(const FtcsPlan &p, int64_t g) {
+    if (p.P == 0) return {kFtcsCanon, p.r, 0.0};
+    const int64_t j = g % p.I, s0 = g - j;
+    const int64_t L = p.total - s0 < p.I ? p.total - s0 : (int64_t)p.I;
+    const int64_t q = j % p.P, end = L < j - q + p.P ? L : j - q + p.P;
+    if (j + 1 < end) return {kFtcsScaled, p.k, 0.0};
+    return {kFtcsClose, p.a[q], p.b[q]};
+}
+#undef HXC_HD
+
 // dst[lo, lo+count) <- `steps` periodic FTCS steps of src (period n),
 // canonical arithmetic.
 cudaError_t heat1d(const double *src, double *dst, int64_t n, int64_t lo, int64_t count,
